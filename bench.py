@@ -1,0 +1,387 @@
+"""Benchmark of the GB300 page-crypto path.
+
+Headline step: AES-256-XTS encryption of a 1 GiB device-resident buffer of
+262,144 x 4096-B sectors (numbered 0..262143), one kernel launch through the
+C ABI.  `value` is GB/s of payload (bytes encrypted / device time).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl kgpu|reference]
+
+N > 1 runs under torchrun: each rank encrypts its own 1 GiB replica (the path
+has no exchange step), timing is max over ranks and `value` is the aggregate.
+`--impl reference` times the CPU oracle on the host cores instead (rank 0 only).
+
+The JSON line also carries: the roofline of the XTS kernel (CUDA-event launch
+time), the oracle's CPU throughput on a bounded sample, an end-to-end number
+through the host-buffer C-ABI call (pinned host pages, copies inside the timed
+region), SM clocks sampled during the timed region, and secondary device-
+resident measurements of the other modes in `extra`.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as w  # noqa: E402
+
+GIB = 1 << 30
+SECTOR = 4096
+METRIC = "AES-256-XTS GB/s (1 GiB on device) vs HBM roofline; batched p50/p99 latency vs per-request"
+WORKLOAD = "AES-256-XTS encrypt, 1 GiB device-resident, 262144 x 4096-B sectors 0..262143, seed 2"
+SMEM_BYTES_PER_CLK_SM = 128  # shared-memory data path per SM per clock (32 banks x 4 B)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="kgpu", choices=["kgpu", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary mode measurements")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--bytes", type=int, default=GIB,
+                    help="buffer size (default 1 GiB; smaller only for profiler captures)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.25)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1305_3345_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(fn.encode())
+            h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "xts256_bulk_1gib_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("csrc_sha256") != csrc_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_oracle_rate(target_s: float = 10.0):
+    """Oracle AES-256-XTS GB/s on a bounded sample of the same workload (the
+    first sectors of the seed-2 buffer), on all host cores."""
+    import oracle
+    key = w.xts_key(2, 256)
+    nthreads = oracle.default_threads()
+    size = 16 << 20
+    data = w.seeded_bytes(2, w.STREAM_DATA, size)
+    t0 = time.perf_counter()
+    oracle.xts(key, 0, data, SECTOR, 0, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    rate = size / dt
+    size = int(min(512 << 20, max(16 << 20, rate * target_s)) // SECTOR * SECTOR)
+    data = w.seeded_bytes(2, w.STREAM_DATA, size)
+    t0 = time.perf_counter()
+    oracle.xts(key, 0, data, SECTOR, 0, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return {"value": size / dt / 1e9, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"first {size // SECTOR} of the 262144 sectors ({size / 2**20:.0f} MiB), "
+                      f"AES-256-XTS encrypt, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    key = w.xts_key(2, 256)
+    nthreads = oracle.default_threads()
+    # one step = the oracle on a bounded sample of the workload (a run of
+    # 4096-B sectors), sized so warm-up + steps stay within a few minutes
+    probe = w.seeded_bytes(2, w.STREAM_DATA, 8 << 20)
+    t0 = time.perf_counter()
+    oracle.xts(key, 0, probe, SECTOR, 0, nthreads=nthreads)
+    rate = probe.size / (time.perf_counter() - t0)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    size = int(min(256 << 20, max(1 << 20, rate * budget)) // SECTOR * SECTOR)
+    data = w.seeded_bytes(2, w.STREAM_DATA, size)
+    out = np.empty_like(data)
+    for _ in range(args.warmup):
+        oracle.xts(key, 0, data, SECTOR, 0, out=out, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.xts(key, 0, data, SECTOR, 0, out=out, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    value = size * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{size // SECTOR} sectors per step"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": nthreads, "kind": "oracle",
+                         "sample": f"{size // SECTOR} x 4096-B sectors ({size / 2**20:.0f} MiB) per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def time_op(fn, iters: int, stream):
+    """Mean CUDA-event time (s) of fn() over iters launches on `stream`."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    fn()
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / iters / 1e3
+
+
+def run_kgpu(args):
+    import torch
+    import paper_1305_3345_gb300 as kg
+
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+
+    ctx = kg.Context(dev)
+    key = w.xts_key(2, 256)
+    kh = ctx.setkey(key, True)
+    nbytes = args.bytes - args.bytes % SECTOR
+    src = torch.from_numpy(w.seeded_bytes(2, w.STREAM_DATA, nbytes)).to(f"cuda:{dev}")
+    dst = torch.empty_like(src)
+
+    def step():
+        ctx.xts_crypt(kh, 0, src, dst, SECTOR, 0, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t_start.record(stream)
+        for a, b in ev:
+            a.record(stream)
+            step()
+            b.record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    launch_s = sum(a.elapsed_time(b) for a, b in ev) / len(ev) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    # the output must be the cipher (a cheap spot check against the oracle)
+    if rank == 0:
+        import oracle
+        for s in (0, nbytes // SECTOR // 2, nbytes // SECTOR - 1):
+            ref = oracle.xts(key, 0, src[s * SECTOR:(s + 1) * SECTOR].cpu().numpy(), SECTOR, s)
+            if not np.array_equal(dst[s * SECTOR:(s + 1) * SECTOR].cpu().numpy(), ref):
+                raise SystemExit(f"bench output mismatch at sector {s}")
+
+    value = world * nbytes * args.steps / elapsed / 1e9
+    props = torch.cuda.get_device_properties(dev)
+    clocks = clk.summary()
+    peaks = measured_peaks()
+
+    # roofline of the dominant kernel (the XTS launch): algorithmic HBM bytes
+    # per launch = 1 GiB read + 1 GiB written
+    hbm_bytes = 2 * nbytes
+    achieved_hbm = hbm_bytes / launch_s / 1e9
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    # shared-memory lookups: Nr = 14 rounds x 16 lookups per 16-B block, plus
+    # one tweak block per 4096-B sector (257 cipher blocks per 256 data blocks)
+    nblocks = nbytes // 16
+    lookups = 14 * 16 * nblocks * (257 / 256)
+    smem_bytes = lookups * 4
+    sm_mhz = clocks["sm_mhz"] or (peaks or {}).get("sm_max_mhz", 2070.0)
+    smem_peak = props.multi_processor_count * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+    achieved_smem = smem_bytes / launch_s / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "smem", "achieved": achieved_smem, "peak": smem_peak, "unit": "GB/s",
+                "frac": achieved_smem / smem_peak, "traffic": traffic,
+                "peak_source": f"{props.multi_processor_count} SMs x 128 B/clk x {sm_mhz:.0f} MHz "
+                               "(median SM clock sampled during the timed region)",
+                "kernel": "bulk_kernel<14,enc,xts>", "launch_ms": launch_s * 1e3}
+    roofline_hbm = {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved_hbm / hbm_peak, "traffic": traffic,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD if nbytes == GIB else f"AES-256-XTS encrypt, {nbytes} B (profiling case)",
+                   "bytes_per_gpu": nbytes, "l2": "inputs larger than L2 (1 GiB vs 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks, "gpu_launches": args.steps,
+    }
+
+    if rank == 0 and not args.no_extra and nbytes == GIB:
+        extra = {}
+        specs = []
+        k128 = ctx.setkey(w.xts_key(2, 128), True)
+        specs.append(("aes256_xts_dec_4k", lambda: ctx.xts_crypt(kh, 1, dst, src, SECTOR, 0, stream)))
+        specs.append(("aes256_xts_enc_512", lambda: ctx.xts_crypt(kh, 0, src, dst, 512, 0, stream)))
+        specs.append(("aes128_xts_enc_4k", lambda: ctx.xts_crypt(k128, 0, src, dst, SECTOR, 0, stream)))
+        specs.append(("aes128_xts_dec_4k", lambda: ctx.xts_crypt(k128, 1, src, dst, SECTOR, 0, stream)))
+        ck = ctx.setkey(w.single_key(2, 128), False)
+        ivs = torch.from_numpy(w.page_ivs(2, GIB // SECTOR).reshape(-1).copy()).to(f"cuda:{dev}")
+        specs.append(("aes128_cbc_dec_4k", lambda: ctx.cbc_decrypt(ck, src, dst, SECTOR, ivs, stream)))
+        specs.append(("aes128_cbc_enc_4k", lambda: ctx.cbc_encrypt_pages(ck, src, dst, SECTOR, ivs, stream)))
+        specs.append(("aes128_ecb_enc", lambda: ctx.ecb_crypt(ck, 0, src, dst, stream)))
+        for name, fn in specs:
+            t = time_op(fn, 20, stream)
+            extra[name] = {"GB/s": GIB / t / 1e9, "ms": t * 1e3}
+        line["extra"] = extra
+        ctx.delkey(k128)
+        ctx.delkey(ck)
+        del ivs
+
+    if rank == 0 and not args.no_e2e and nbytes == GIB:
+        # end to end through the host-buffer call: 1 GiB pinned in, 1 GiB out,
+        # chunked copy/compute pipeline inside the library
+        hsrc = torch.empty(GIB, dtype=torch.uint8).pin_memory()
+        hsrc.copy_(src.cpu())
+        hdst = torch.empty(GIB, dtype=torch.uint8).pin_memory()
+        chunk = 64 << 20
+        ctx.xts_crypt_host(kh, 0, hsrc, hdst, SECTOR, 0, chunk)
+        e2e_steps = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.xts_crypt_host(kh, 0, hsrc, hdst, SECTOR, 0, chunk)
+        dt = (time.perf_counter() - t0) / e2e_steps
+        import oracle
+        for sct in (0, 262143):
+            ref = oracle.xts(key, 0, hsrc[sct * SECTOR:(sct + 1) * SECTOR].numpy(), SECTOR, sct)
+            if not np.array_equal(hdst[sct * SECTOR:(sct + 1) * SECTOR].numpy(), ref):
+                raise SystemExit(f"e2e output mismatch at sector {sct}")
+        line["e2e"] = {"value": GIB / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": GIB,
+                       "d2h_bytes_per_step": GIB, "steps": e2e_steps, "chunk_bytes": chunk,
+                       "call": "kgpu_aes_xts_crypt_host (pinned host pages)"}
+        del hsrc, hdst
+
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate()
+
+    ctx.delkey(kh)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kgpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * kgpu.h -- C ABI of the GB300 page-crypto service.
+ *
+ * The service follows the request model of "Augmenting Operating Systems With
+ * the GPU" (section 3.2, the GLinux architecture): a caller hands the GPU
+ * page-sized buffers together with a key and the sector or IV numbering, and
+ * gets the transformed pages back, either by waiting on its own CUDA stream or
+ * through a submit/poll ticket (the paper's request queue / response queue with
+ * blocking or busy-waiting).  The cipher service itself is the paper's GPU AES
+ * (section 3.3), extended from ECB to the page modes that encrypted storage
+ * uses: XTS (IEEE 1619-2007 / NIST SP 800-38E) and CBC (NIST SP 800-38A).
+ *
+ * Conventions for every call:
+ *  - Return value: 0 (KGPU_OK) or a negative errno-style code (KGPU_E*).
+ *    Nothing is launched when a call returns an error.
+ *  - Buffers are caller-owned; the library never frees caller memory.  Unless a
+ *    call says otherwise, src/dst/ivs are DEVICE pointers (cudaMalloc, the
+ *    PyTorch caching allocator, or managed memory) and must lie wholly inside
+ *    one device allocation; this is checked, and a failure is KGPU_EFAULT.
+ *  - src and dst must be 16-byte aligned.  src == dst (in place) is allowed
+ *    for every mode; any other overlap is KGPU_EINVAL.
+ *  - Lengths are in bytes and must be whole data units / pages; the unit size
+ *    must be a nonzero multiple of 16.  There is no padding and no ciphertext
+ *    stealing.  len == 0 is a no-op.
+ *  - Device work is asynchronous on the caller's stream (0 = legacy default
+ *    stream).  A launch failure is reported as KGPU_EIO; an asynchronous fault
+ *    surfaces from the next synchronising CUDA call on that stream.
+ *  - A context is bound to one device.  Calls on one context may come from
+ *    several host threads; key handles are shared by all of them.
+ */
+#ifndef KGPU_H
+#define KGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#pragma GCC visibility push(default) /* the library is built with hidden visibility */
+#endif
+
+typedef struct kgpu_ctx kgpu_ctx;  /* opaque, library-owned */
+typedef uint32_t kgpu_key;         /* handle into the context's key table */
+typedef uint64_t kgpu_ticket;      /* handle of a submitted batch */
+typedef struct CUstream_st *kgpu_stream; /* a cudaStream_t */
+
+enum {
+    KGPU_OK = 0,
+    KGPU_EIO = -5,         /* CUDA launch or runtime failure */
+    KGPU_ENOMEM = -12,     /* allocation failed or a table is full */
+    KGPU_EFAULT = -14,     /* a pointer is not (wholly) inside a usable allocation */
+    KGPU_EBUSY = -16,      /* queue full / admission refused: retry later */
+    KGPU_ENODEV = -19,     /* no such CUDA device, or not an sm_103 part */
+    KGPU_EINVAL = -22,     /* malformed argument (length, alignment, key, mode) */
+    KGPU_ENOENT = -2,      /* unknown key handle or ticket */
+    KGPU_ETIMEDOUT = -110  /* a bounded wait ran out */
+};
+
+enum { KGPU_ENCRYPT = 0, KGPU_DECRYPT = 1 };
+
+enum {
+    KGPU_MODE_XTS = 0,     /* XTS, direction from kgpu_request.dir */
+    KGPU_MODE_CBC_DEC = 1, /* CBC decryption, parallel over blocks */
+    KGPU_MODE_CBC_ENC = 2, /* CBC encryption, parallel over pages */
+    KGPU_MODE_ECB = 3      /* ECB, the paper's own service mode (section 3.3) */
+};
+
+/* Library version, (major << 16) | minor. */
+int kgpu_version(void);
+
+/* Short English description of a KGPU_* code (static storage). */
+const char *kgpu_strerror(int code);
+
+/* Optional configuration; zero fields take defaults. */
+typedef struct kgpu_config {
+    uint32_t max_keys;            /* key-table capacity (default 4096) */
+    uint32_t ring_slots;          /* serving ring capacity (default 4096, power of two) */
+    uint64_t admit_bytes;         /* serving: cap on bytes in flight (default 8 GiB) */
+    uint64_t idle_timeout_ns;     /* serving kernel exits after this long with no work (default 2 s) */
+    uint32_t reserved[8];
+} kgpu_config;
+
+/*
+ * Create a context on CUDA device `device` (uploads the cipher tables and
+ * allocates the device key table).  cfg may be NULL.  The context owns no
+ * caller memory.  Errors: KGPU_ENODEV, KGPU_ENOMEM, KGPU_EIO, KGPU_EINVAL.
+ */
+int kgpu_init(kgpu_ctx **ctx, int device, const kgpu_config *cfg);
+
+/* Stop the serving kernel if one runs, wait for the context's own work and
+ * free everything the context allocated.  NULL is accepted. */
+int kgpu_destroy(kgpu_ctx *ctx);
+
+/*
+ * Register a key (the paper's pre-loaded service state, section 3.1).  The key
+ * schedule is expanded on the host (FIPS-197 section 5.2) and stored in the
+ * context, both for launch-time use and in the device key table read by the
+ * batched and serving kernels.
+ *   xts = 0: a single AES key of 16, 24 or 32 bytes (CBC, ECB).
+ *   xts = 1: Key1 || Key2 of 32 or 64 bytes (XTS data key, then tweak key;
+ *            IEEE 1619 defines XTS-AES-128 and XTS-AES-256 only);
+ *            Key1 == Key2 is rejected (IEEE 1619-2018 requires them distinct).
+ * The key bytes are copied; the caller may wipe its buffer after the call.
+ * Errors: KGPU_EINVAL (length, duplicated halves), KGPU_ENOMEM (table full).
+ */
+int kgpu_aes_setkey(kgpu_ctx *ctx, const uint8_t *key, size_t key_len, int xts, kgpu_key *out);
+
+/* Forget a key.  Work already submitted with it completes first. */
+int kgpu_aes_delkey(kgpu_ctx *ctx, kgpu_key key);
+
+/*
+ * XTS-AES over len / du_size data units (IEEE 1619 section 5.3 / 5.4):
+ * unit u is numbered first_sector + u, its tweak is E_Key2(number) with the
+ * number as a 128-bit little-endian value, and block j of the unit is
+ * processed with tweak * alpha^j in GF(2^128).  dir: KGPU_ENCRYPT / DECRYPT.
+ * du_size: any nonzero multiple of 16 (512 and 4096 are the usual sectors).
+ * src, dst: device pointers, len bytes each.  Async on `stream`.
+ * Errors: KGPU_EINVAL, KGPU_ENOENT (not an XTS key), KGPU_EFAULT, KGPU_EIO.
+ */
+int kgpu_aes_xts_crypt(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,
+                       size_t du_size, uint64_t first_sector, kgpu_stream stream);
+
+/*
+ * CBC decryption, one chain per page (NIST SP 800-38A 6.2):
+ *   P_0 = D_K(C_0) ^ IV_page,  P_i = D_K(C_i) ^ C_{i-1}.
+ * Every block is independent given C_{i-1}, so the kernel runs one block per
+ * thread.  ivs: DEVICE pointer to len / page_size IVs of 16 bytes.
+ * page_size: nonzero multiple of 16 (4096 for file pages).
+ */
+int kgpu_aes_cbc_decrypt(kgpu_ctx *ctx, kgpu_key key, const void *src, void *dst, size_t len,
+                         size_t page_size, const uint8_t *ivs, kgpu_stream stream);
+
+/*
+ * CBC encryption, one chain per page: C_0 = E_K(P_0 ^ IV_page),
+ * C_i = E_K(P_i ^ C_{i-1}).  Sequential inside a page, parallel across pages
+ * (one thread per page).  Arguments as kgpu_aes_cbc_decrypt.
+ */
+int kgpu_aes_cbc_encrypt_pages(kgpu_ctx *ctx, kgpu_key key, const void *src, void *dst, size_t len,
+                               size_t page_size, const uint8_t *ivs, kgpu_stream stream);
+
+/*
+ * ECB over len / 16 independent blocks: the mode of the paper's own GPU AES
+ * service (section 3.3).  key: a single (non-XTS) key.
+ */
+int kgpu_aes_ecb_crypt(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,
+                       kgpu_stream stream);
+
+/*
+ * XTS over HOST-resident pages, the paper's pinned-buffer pipeline (section
+ * 3.1, "Data Copy Overhead", and the buffer rotation of section 3.2): the
+ * buffer is cut into chunk_bytes pieces (a multiple of du_size; 0 = 4 MiB),
+ * and each piece is copied host-to-device, transformed and copied back on one
+ * of three library-owned streams (one chunk in, one transformed, one out), so
+ * copies overlap compute.  src and dst are
+ * HOST pointers (pinned memory gives full link speed; pageable memory works
+ * but is slower); src == dst is allowed.  Blocks until dst holds the result.
+ * Device staging buffers are owned by the context and reused across calls.
+ */
+int kgpu_aes_xts_crypt_host(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,
+                            size_t du_size, uint64_t first_sector, size_t chunk_bytes);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KGPU_H */

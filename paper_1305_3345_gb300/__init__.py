@@ -1,0 +1,249 @@
+"""Python binding of the kgpu C ABI (include/kgpu.h): GB300 page crypto.
+
+This layer only marshals arguments (torch tensors / numpy arrays -> pointers and
+sizes, torch streams -> cudaStream_t) and turns negative return codes into
+exceptions.  Every byte of every transform is computed by the CUDA kernels in
+libkgpu.so; there is no Python or CPU fallback -- if the library cannot be built
+or loaded, every call raises.
+
+The function names are those of the C ABI.  `Context` is a small convenience
+wrapper that owns a kgpu_ctx.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build as _build
+
+ENCRYPT = 0
+DECRYPT = 1
+MODE_XTS = 0
+MODE_CBC_DEC = 1
+MODE_CBC_ENC = 2
+MODE_ECB = 3
+
+_ERRORS = {
+    -5: "EIO", -12: "ENOMEM", -14: "EFAULT", -16: "EBUSY", -19: "ENODEV", -22: "EINVAL", -2: "ENOENT",
+    -110: "ETIMEDOUT",
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KgpuError(RuntimeError):
+    def __init__(self, rc: int, what: str):
+        self.rc = rc
+        self.code = _ERRORS.get(rc, str(rc))
+        super().__init__(f"{what} failed: {self.code} ({rc})")
+
+
+class KgpuConfig(ctypes.Structure):
+    _fields_ = [("max_keys", ctypes.c_uint32), ("ring_slots", ctypes.c_uint32),
+                ("admit_bytes", ctypes.c_uint64), ("idle_timeout_ns", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint32 * 8)]
+
+
+def ensure_built() -> str:
+    """Build libkgpu.so in-tree if it is missing or stale; return its path."""
+    return _build.build()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded C library (built on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(ensure_built())
+            vp, sz, u64, i32, u32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+            sig = {
+                "kgpu_version": ([], i32),
+                "kgpu_strerror": ([i32], ctypes.c_char_p),
+                "kgpu_init": ([ctypes.POINTER(vp), i32, vp], i32),
+                "kgpu_destroy": ([vp], i32),
+                "kgpu_aes_setkey": ([vp, vp, sz, i32, ctypes.POINTER(u32)], i32),
+                "kgpu_aes_delkey": ([vp, u32], i32),
+                "kgpu_aes_xts_crypt": ([vp, u32, i32, vp, vp, sz, sz, u64, vp], i32),
+                "kgpu_aes_cbc_decrypt": ([vp, u32, vp, vp, sz, sz, vp, vp], i32),
+                "kgpu_aes_cbc_encrypt_pages": ([vp, u32, vp, vp, sz, sz, vp, vp], i32),
+                "kgpu_aes_ecb_crypt": ([vp, u32, i32, vp, vp, sz, vp], i32),
+                "kgpu_aes_xts_crypt_host": ([vp, u32, i32, vp, vp, sz, sz, u64, sz], i32),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise KgpuError(rc, what)
+    return rc
+
+
+def _dev_buf(t):
+    """(pointer, nbytes) of a contiguous uint8 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch.Tensor")
+    if t.dtype != torch.uint8 or not t.is_contiguous():
+        raise TypeError("expected a contiguous uint8 tensor")
+    return t.data_ptr(), t.numel()
+
+
+def _host_buf(a):
+    """(pointer, nbytes) of a contiguous uint8 host buffer (numpy or CPU tensor)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.uint8 or not a.is_contiguous():
+                raise TypeError("expected a contiguous uint8 CPU tensor")
+            return a.data_ptr(), a.numel()
+    except ImportError:
+        pass
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a contiguous uint8 numpy array")
+    return a.ctypes.data, a.size
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------- C-ABI mirrors
+
+def kgpu_version() -> int:
+    return lib().kgpu_version()
+
+
+def kgpu_strerror(code: int) -> str:
+    return lib().kgpu_strerror(code).decode()
+
+
+def kgpu_init(device: int = 0, cfg: KgpuConfig | None = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().kgpu_init(ctypes.byref(ctx), device, ctypes.byref(cfg) if cfg is not None else None),
+           "kgpu_init")
+    return ctx
+
+
+def kgpu_destroy(ctx) -> None:
+    _check(lib().kgpu_destroy(ctx), "kgpu_destroy")
+
+
+def kgpu_aes_setkey(ctx, key: bytes, xts: bool) -> int:
+    h = ctypes.c_uint32()
+    kb = ctypes.create_string_buffer(bytes(key), len(key))
+    _check(lib().kgpu_aes_setkey(ctx, kb, len(key), 1 if xts else 0, ctypes.byref(h)), "kgpu_aes_setkey")
+    return h.value
+
+
+def kgpu_aes_delkey(ctx, key: int) -> None:
+    _check(lib().kgpu_aes_delkey(ctx, key), "kgpu_aes_delkey")
+
+
+def kgpu_aes_xts_crypt(ctx, key: int, dir: int, src, dst, du_size: int, first_sector: int = 0,
+                       stream=None) -> None:
+    sp, n = _dev_buf(src)
+    dp, m = _dev_buf(dst)
+    if n != m:
+        raise ValueError("src and dst sizes differ")
+    _check(lib().kgpu_aes_xts_crypt(ctx, key, dir, sp, dp, n, du_size, first_sector, _stream(stream)),
+           "kgpu_aes_xts_crypt")
+
+
+def kgpu_aes_cbc_decrypt(ctx, key: int, src, dst, page_size: int, ivs, stream=None) -> None:
+    sp, n = _dev_buf(src)
+    dp, m = _dev_buf(dst)
+    ip, _ = _dev_buf(ivs)
+    if n != m:
+        raise ValueError("src and dst sizes differ")
+    _check(lib().kgpu_aes_cbc_decrypt(ctx, key, sp, dp, n, page_size, ip, _stream(stream)),
+           "kgpu_aes_cbc_decrypt")
+
+
+def kgpu_aes_cbc_encrypt_pages(ctx, key: int, src, dst, page_size: int, ivs, stream=None) -> None:
+    sp, n = _dev_buf(src)
+    dp, m = _dev_buf(dst)
+    ip, _ = _dev_buf(ivs)
+    if n != m:
+        raise ValueError("src and dst sizes differ")
+    _check(lib().kgpu_aes_cbc_encrypt_pages(ctx, key, sp, dp, n, page_size, ip, _stream(stream)),
+           "kgpu_aes_cbc_encrypt_pages")
+
+
+def kgpu_aes_ecb_crypt(ctx, key: int, dir: int, src, dst, stream=None) -> None:
+    sp, n = _dev_buf(src)
+    dp, m = _dev_buf(dst)
+    if n != m:
+        raise ValueError("src and dst sizes differ")
+    _check(lib().kgpu_aes_ecb_crypt(ctx, key, dir, sp, dp, n, _stream(stream)), "kgpu_aes_ecb_crypt")
+
+
+def kgpu_aes_xts_crypt_host(ctx, key: int, dir: int, src, dst, du_size: int, first_sector: int = 0,
+                            chunk_bytes: int = 0) -> None:
+    sp, n = _host_buf(src)
+    dp, m = _host_buf(dst)
+    if n != m:
+        raise ValueError("src and dst sizes differ")
+    _check(lib().kgpu_aes_xts_crypt_host(ctx, key, dir, sp, dp, n, du_size, first_sector, chunk_bytes),
+           "kgpu_aes_xts_crypt_host")
+
+
+class Context:
+    """Owns one kgpu_ctx on a device; methods mirror the C ABI without the ctx."""
+
+    def __init__(self, device: int = 0, cfg: KgpuConfig | None = None):
+        self.device = device
+        self.handle = kgpu_init(device, cfg)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            kgpu_destroy(self.handle)
+        self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def setkey(self, key: bytes, xts: bool) -> int:
+        return kgpu_aes_setkey(self.handle, key, xts)
+
+    def delkey(self, key: int) -> None:
+        kgpu_aes_delkey(self.handle, key)
+
+    def xts_crypt(self, key, dir, src, dst, du_size, first_sector=0, stream=None):
+        kgpu_aes_xts_crypt(self.handle, key, dir, src, dst, du_size, first_sector, stream)
+
+    def cbc_decrypt(self, key, src, dst, page_size, ivs, stream=None):
+        kgpu_aes_cbc_decrypt(self.handle, key, src, dst, page_size, ivs, stream)
+
+    def cbc_encrypt_pages(self, key, src, dst, page_size, ivs, stream=None):
+        kgpu_aes_cbc_encrypt_pages(self.handle, key, src, dst, page_size, ivs, stream)
+
+    def ecb_crypt(self, key, dir, src, dst, stream=None):
+        kgpu_aes_ecb_crypt(self.handle, key, dir, src, dst, stream)
+
+    def xts_crypt_host(self, key, dir, src, dst, du_size, first_sector=0, chunk_bytes=0):
+        kgpu_aes_xts_crypt_host(self.handle, key, dir, src, dst, du_size, first_sector, chunk_bytes)

@@ -1,0 +1,428 @@
+// C-ABI entry points (include/kgpu.h): context, key table, argument checks and
+// the synchronous-looking host-resident pipeline.  Every transform itself runs
+// in the CUDA kernels of kgpu_bulk.cu; this file only validates and launches.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "aes_tables_host.h"
+#include "kgpu_internal.h"
+
+using namespace kgpu;
+
+struct kgpu_ctx {
+    int device = 0;
+    int num_sms = 0;
+    kgpu_config cfg{};
+    std::mutex mu;
+    std::vector<HostKey> keys;
+    DevKey* d_keys = nullptr;
+
+    // host-resident pipeline (kgpu_aes_xts_crypt_host): three device staging
+    // buffers on three streams -- one chunk being copied in, one transformed,
+    // one copied out (the GPU-side triple buffering of the paper's section 3.2)
+    static constexpr int kStages = 3;
+    std::mutex host_mu;
+    cudaStream_t hs[kStages] = {};
+    uint8_t* staging[kStages] = {};
+    size_t staging_bytes = 0;
+};
+
+namespace {
+
+constexpr int kVersion = (0 << 16) | 3;
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev_);
+        if (prev_ != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != prev_) cudaSetDevice(prev_);
+    }
+
+  private:
+    int prev_ = 0;
+};
+
+int from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return KGPU_OK;
+    if (e == cudaErrorMemoryAllocation) return KGPU_ENOMEM;
+    return KGPU_EIO;
+}
+
+// cuMemGetAddressRange through the runtime's driver entry-point table, so the
+// library has no link-time dependency on libcuda (it loads on GPU-less hosts).
+typedef CUresult (*AddressRangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
+
+AddressRangeFn address_range_fn() {
+    static AddressRangeFn fn = []() -> AddressRangeFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<AddressRangeFn>(f);
+    }();
+    return fn;
+}
+
+// [p, p + len) must be device (or managed) memory of ctx's device, inside one
+// allocation.
+int check_device_range(const kgpu_ctx* ctx, const void* p, size_t len) {
+    if (!p) return KGPU_EFAULT;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EFAULT;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return KGPU_EFAULT;
+    if (a.type == cudaMemoryTypeDevice && a.device != ctx->device) return KGPU_EFAULT;
+    CUdeviceptr base = 0;
+    size_t size = 0;
+    AddressRangeFn range = address_range_fn();
+    if (!range || range(&base, &size, (CUdeviceptr)p) != CUDA_SUCCESS) return KGPU_EFAULT;
+    uintptr_t end = (uintptr_t)p + len;
+    if (end < (uintptr_t)p || end > (uintptr_t)base + size) return KGPU_EFAULT;
+    return KGPU_OK;
+}
+
+int check_host_ptr(const void* p) {
+    if (!p) return KGPU_EFAULT;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EFAULT;
+    }
+    if (a.type == cudaMemoryTypeDevice) return KGPU_EFAULT;
+    return KGPU_OK;
+}
+
+// src == dst, or disjoint; 16-byte aligned.
+int check_pair(const void* src, const void* dst, size_t len) {
+    uintptr_t s = (uintptr_t)src, d = (uintptr_t)dst;
+    if ((s | d) & 15) return KGPU_EINVAL;
+    if (s != d && s < d + len && d < s + len) return KGPU_EINVAL;
+    return KGPU_OK;
+}
+
+int get_key(kgpu_ctx* ctx, kgpu_key h, bool want_xts, HostKey* out) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (h == 0 || h > ctx->keys.size()) return KGPU_ENOENT;
+    const HostKey& k = ctx->keys[h - 1];
+    if (!k.live || k.xts != want_xts) return KGPU_ENOENT;
+    *out = k;
+    return KGPU_OK;
+}
+
+int xts_args(kgpu_ctx* ctx, int dir, size_t len, size_t du, uint64_t first_sector) {
+    if (!ctx) return KGPU_EINVAL;
+    if (dir != KGPU_ENCRYPT && dir != KGPU_DECRYPT) return KGPU_EINVAL;
+    if (du == 0 || du % 16 || len % du) return KGPU_EINVAL;
+    if (du / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
+    uint64_t units = len / du;
+    if (units && first_sector + (units - 1) < first_sector) return KGPU_EINVAL;  // 64-bit unit numbers
+    return KGPU_OK;
+}
+
+void fill_bulk(BulkParams* p, const HostKey& k, int dir, const void* src, void* dst, size_t len, size_t du,
+               uint64_t first_sector) {
+    std::memset(p, 0, sizeof(*p));
+    p->src = static_cast<const uint4*>(src);
+    p->dst = static_cast<uint4*>(dst);
+    p->nblocks = len / 16;
+    p->bps = (uint32_t)(du / 16);
+    p->first_sector = first_sector;
+    std::memcpy(p->rk, dir == KGPU_ENCRYPT ? k.enc : k.dec, sizeof(p->rk));
+    std::memcpy(p->tk, k.twk, sizeof(p->tk));
+}
+
+}  // namespace
+
+extern "C" {
+
+int kgpu_version(void) { return kVersion; }
+
+const char* kgpu_strerror(int code) {
+    switch (code) {
+        case KGPU_OK: return "success";
+        case KGPU_EIO: return "CUDA launch or runtime failure";
+        case KGPU_ENOMEM: return "out of memory or table full";
+        case KGPU_EFAULT: return "pointer not inside a usable allocation";
+        case KGPU_EBUSY: return "busy: queue full or admission refused";
+        case KGPU_ENODEV: return "no usable sm_103 CUDA device";
+        case KGPU_EINVAL: return "invalid argument";
+        case KGPU_ENOENT: return "unknown key or ticket";
+        case KGPU_ETIMEDOUT: return "bounded wait timed out";
+        default: return "unknown error";
+    }
+}
+
+int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
+    if (!out) return KGPU_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return KGPU_ENODEV;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return KGPU_ENODEV;
+    if (prop.major != 10 || prop.minor != 3) return KGPU_ENODEV;  // built for sm_103a only
+    int reserved = -1;
+    if (cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess ||
+        reserved != kSmemReservedBytes)
+        return KGPU_ENODEV;  // the kernels' shared-memory offsets assume this layout
+    kgpu_ctx* ctx = new (std::nothrow) kgpu_ctx();
+    if (!ctx) return KGPU_ENOMEM;
+    ctx->device = device;
+    ctx->num_sms = prop.multiProcessorCount;
+    if (cfg) ctx->cfg = *cfg;
+    if (!ctx->cfg.max_keys) ctx->cfg.max_keys = 4096;
+    if (!ctx->cfg.ring_slots) ctx->cfg.ring_slots = 4096;
+    if (!ctx->cfg.admit_bytes) ctx->cfg.admit_bytes = 8ull << 30;
+    if (!ctx->cfg.idle_timeout_ns) ctx->cfg.idle_timeout_ns = 2000000000ull;
+    if (ctx->cfg.max_keys > (1u << 20) || (ctx->cfg.ring_slots & (ctx->cfg.ring_slots - 1))) {
+        delete ctx;
+        return KGPU_EINVAL;
+    }
+
+    DeviceGuard g(device);
+    host::Tables t;
+    host::make_tables(&t);
+    int rc = from_cuda(configure_kernels());
+    if (rc == KGPU_OK) rc = from_cuda(upload_tables(t.te0, t.td0, t.isb4));
+    if (rc == KGPU_OK) rc = from_cuda(cudaMalloc(&ctx->d_keys, sizeof(DevKey) * ctx->cfg.max_keys));
+    if (rc == KGPU_OK) rc = from_cuda(cudaMemset(ctx->d_keys, 0, sizeof(DevKey) * ctx->cfg.max_keys));
+    if (rc != KGPU_OK) {
+        cudaGetLastError();
+        kgpu_destroy(ctx);
+        return rc;
+    }
+    ctx->keys.reserve(64);
+    *out = ctx;
+    return KGPU_OK;
+}
+
+int kgpu_destroy(kgpu_ctx* ctx) {
+    if (!ctx) return KGPU_OK;
+    {
+        DeviceGuard g(ctx->device);
+        for (int i = 0; i < kgpu_ctx::kStages; i++) {
+            if (ctx->hs[i]) {
+                cudaStreamSynchronize(ctx->hs[i]);
+                cudaStreamDestroy(ctx->hs[i]);
+            }
+            if (ctx->staging[i]) cudaFree(ctx->staging[i]);
+        }
+        if (ctx->d_keys) cudaFree(ctx->d_keys);
+    }
+    delete ctx;
+    return KGPU_OK;
+}
+
+int kgpu_aes_setkey(kgpu_ctx* ctx, const uint8_t* key, size_t key_len, int xts, kgpu_key* out) {
+    if (!ctx || !key || !out || (xts != 0 && xts != 1)) return KGPU_EINVAL;
+    HostKey hk;
+    hk.live = true;
+    hk.xts = xts == 1;
+    std::memset(hk.enc, 0, sizeof(hk.enc));
+    std::memset(hk.dec, 0, sizeof(hk.dec));
+    std::memset(hk.twk, 0, sizeof(hk.twk));
+    size_t half = key_len;
+    if (hk.xts) {
+        // IEEE 1619 defines XTS-AES-128 and XTS-AES-256 only
+        if (key_len != 32 && key_len != 64) return KGPU_EINVAL;
+        half = key_len / 2;
+        if (std::memcmp(key, key + half, half) == 0) return KGPU_EINVAL;
+    }
+    hk.nr = host::expand_key(key, half, hk.enc);
+    if (!hk.nr) return KGPU_EINVAL;
+    host::decrypt_schedule(hk.enc, hk.nr, hk.dec);
+    if (hk.xts && host::expand_key(key + half, half, hk.twk) != hk.nr) return KGPU_EINVAL;
+
+    DevKey dk;
+    std::memset(&dk, 0, sizeof(dk));
+    std::memcpy(dk.enc, hk.enc, sizeof(dk.enc));
+    std::memcpy(dk.dec, hk.dec, sizeof(dk.dec));
+    std::memcpy(dk.twk, hk.twk, sizeof(dk.twk));
+    dk.nr = (uint32_t)hk.nr;
+    dk.flags = (hk.xts ? 1u : 0u) | 2u;
+
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    size_t slot = ctx->keys.size();
+    for (size_t i = 0; i < ctx->keys.size(); i++) {
+        if (!ctx->keys[i].live) {
+            slot = i;
+            break;
+        }
+    }
+    if (slot >= ctx->cfg.max_keys) return KGPU_ENOMEM;
+    DeviceGuard g(ctx->device);
+    if (cudaMemcpy(ctx->d_keys + slot, &dk, sizeof(dk), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    if (slot == ctx->keys.size()) ctx->keys.push_back(hk);
+    else ctx->keys[slot] = hk;
+    *out = (kgpu_key)(slot + 1);
+    std::memset(&dk, 0, sizeof(dk));
+    return KGPU_OK;
+}
+
+int kgpu_aes_delkey(kgpu_ctx* ctx, kgpu_key key) {
+    if (!ctx) return KGPU_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (key == 0 || key > ctx->keys.size() || !ctx->keys[key - 1].live) return KGPU_ENOENT;
+    DeviceGuard g(ctx->device);
+    // Device-side uses of the key are ordered before this by the device-wide
+    // synchronisation; the record is then wiped.
+    cudaDeviceSynchronize();
+    DevKey zero;
+    std::memset(&zero, 0, sizeof(zero));
+    cudaMemcpy(ctx->d_keys + (key - 1), &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    std::memset(&ctx->keys[key - 1], 0, sizeof(HostKey));
+    ctx->keys[key - 1].live = false;
+    return KGPU_OK;
+}
+
+int kgpu_aes_xts_crypt(kgpu_ctx* ctx, kgpu_key key, int dir, const void* src, void* dst, size_t len,
+                       size_t du_size, uint64_t first_sector, kgpu_stream stream) {
+    int rc = xts_args(ctx, dir, len, du_size, first_sector);
+    if (rc) return rc;
+    HostKey k;
+    if ((rc = get_key(ctx, key, true, &k))) return rc;
+    if (len == 0) return KGPU_OK;
+    if ((rc = check_pair(src, dst, len))) return rc;
+    if ((rc = check_device_range(ctx, src, len)) || (rc = check_device_range(ctx, dst, len))) return rc;
+    BulkParams p;
+    fill_bulk(&p, k, dir, src, dst, len, du_size, first_sector);
+    DeviceGuard g(ctx->device);
+    return from_cuda(launch_xts(p, k.nr, dir, ctx->num_sms, (cudaStream_t)stream));
+}
+
+int kgpu_aes_ecb_crypt(kgpu_ctx* ctx, kgpu_key key, int dir, const void* src, void* dst, size_t len,
+                       kgpu_stream stream) {
+    if (!ctx || (dir != KGPU_ENCRYPT && dir != KGPU_DECRYPT) || len % 16) return KGPU_EINVAL;
+    HostKey k;
+    int rc = get_key(ctx, key, false, &k);
+    if (rc) return rc;
+    if (len == 0) return KGPU_OK;
+    if ((rc = check_pair(src, dst, len))) return rc;
+    if ((rc = check_device_range(ctx, src, len)) || (rc = check_device_range(ctx, dst, len))) return rc;
+    BulkParams p;
+    fill_bulk(&p, k, dir, src, dst, len, 16, 0);
+    DeviceGuard g(ctx->device);
+    return from_cuda(launch_ecb(p, k.nr, dir, ctx->num_sms, (cudaStream_t)stream));
+}
+
+static int cbc_common(kgpu_ctx* ctx, kgpu_key key, bool enc, const void* src, void* dst, size_t len,
+                      size_t page, const uint8_t* ivs, kgpu_stream stream) {
+    if (!ctx || page == 0 || page % 16 || len % page || page / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
+    HostKey k;
+    int rc = get_key(ctx, key, false, &k);
+    if (rc) return rc;
+    if (len == 0) return KGPU_OK;
+    if ((rc = check_pair(src, dst, len))) return rc;
+    if ((uintptr_t)ivs & 15) return KGPU_EINVAL;
+    size_t npages = len / page;
+    if ((rc = check_device_range(ctx, src, len)) || (rc = check_device_range(ctx, dst, len)) ||
+        (rc = check_device_range(ctx, ivs, npages * 16)))
+        return rc;
+    // the IVs must not be overwritten while pages are being processed
+    uintptr_t iv0 = (uintptr_t)ivs, iv1 = iv0 + npages * 16, d0 = (uintptr_t)dst;
+    if (iv0 < d0 + len && d0 < iv1) return KGPU_EINVAL;
+    CbcParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.src = static_cast<const uint4*>(src);
+    p.dst = static_cast<uint4*>(dst);
+    p.ivs = reinterpret_cast<const uint4*>(ivs);
+    p.npages = npages;
+    p.bpp = (uint32_t)(page / 16);
+    std::memcpy(p.rk, enc ? k.enc : k.dec, sizeof(p.rk));
+    DeviceGuard g(ctx->device);
+    cudaError_t e = enc ? launch_cbc_enc(p, k.nr, ctx->num_sms, (cudaStream_t)stream)
+                        : launch_cbc_dec(p, k.nr, ctx->num_sms, (cudaStream_t)stream);
+    return from_cuda(e);
+}
+
+int kgpu_aes_cbc_decrypt(kgpu_ctx* ctx, kgpu_key key, const void* src, void* dst, size_t len, size_t page_size,
+                         const uint8_t* ivs, kgpu_stream stream) {
+    return cbc_common(ctx, key, false, src, dst, len, page_size, ivs, stream);
+}
+
+int kgpu_aes_cbc_encrypt_pages(kgpu_ctx* ctx, kgpu_key key, const void* src, void* dst, size_t len,
+                               size_t page_size, const uint8_t* ivs, kgpu_stream stream) {
+    return cbc_common(ctx, key, true, src, dst, len, page_size, ivs, stream);
+}
+
+int kgpu_aes_xts_crypt_host(kgpu_ctx* ctx, kgpu_key key, int dir, const void* src, void* dst, size_t len,
+                            size_t du_size, uint64_t first_sector, size_t chunk_bytes) {
+    int rc = xts_args(ctx, dir, len, du_size, first_sector);
+    if (rc) return rc;
+    HostKey k;
+    if ((rc = get_key(ctx, key, true, &k))) return rc;
+    if (len == 0) return KGPU_OK;
+    if ((rc = check_pair(src, dst, len))) return rc;
+    if ((rc = check_host_ptr(src)) || (rc = check_host_ptr(dst))) return rc;
+    size_t chunk = chunk_bytes ? chunk_bytes : (4u << 20);
+    if (chunk < du_size) chunk = du_size;
+    chunk -= chunk % du_size;
+    if (chunk > len) chunk = len;
+
+    std::lock_guard<std::mutex> lk(ctx->host_mu);
+    DeviceGuard g(ctx->device);
+    for (int i = 0; i < kgpu_ctx::kStages; i++) {
+        if (!ctx->hs[i] && cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking) != cudaSuccess)
+            return KGPU_EIO;
+    }
+    if (ctx->staging_bytes < chunk) {
+        for (int i = 0; i < kgpu_ctx::kStages; i++) {
+            cudaStreamSynchronize(ctx->hs[i]);
+            if (ctx->staging[i]) cudaFree(ctx->staging[i]);
+            ctx->staging[i] = nullptr;
+        }
+        ctx->staging_bytes = 0;
+        for (int i = 0; i < kgpu_ctx::kStages; i++) {
+            if (cudaMalloc(&ctx->staging[i], chunk) != cudaSuccess) {
+                cudaGetLastError();
+                return KGPU_ENOMEM;
+            }
+        }
+        ctx->staging_bytes = chunk;
+    }
+    const uint8_t* s = static_cast<const uint8_t*>(src);
+    uint8_t* d = static_cast<uint8_t*>(dst);
+    cudaError_t e = cudaSuccess;
+    size_t idx = 0;
+    for (size_t off = 0; off < len && e == cudaSuccess; off += chunk, idx++) {
+        int st = (int)(idx % kgpu_ctx::kStages);
+        size_t n = len - off < chunk ? len - off : chunk;
+        cudaStream_t hs = ctx->hs[st];
+        // In-order streams: this H2D waits for the D2H that last used the buffer.
+        e = cudaMemcpyAsync(ctx->staging[st], s + off, n, cudaMemcpyHostToDevice, hs);
+        if (e != cudaSuccess) break;
+        BulkParams p;
+        fill_bulk(&p, k, dir, ctx->staging[st], ctx->staging[st], n, du_size, first_sector + off / du_size);
+        e = launch_xts(p, k.nr, dir, ctx->num_sms, hs);
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(d + off, ctx->staging[st], n, cudaMemcpyDeviceToHost, hs);
+    }
+    for (int i = 0; i < kgpu_ctx::kStages; i++) {
+        cudaError_t e2 = cudaStreamSynchronize(ctx->hs[i]);
+        if (e == cudaSuccess) e = e2;
+    }
+    return from_cuda(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,356 @@
+// Bulk device-resident kernels: XTS (IEEE 1619), ECB, CBC decrypt (parallel
+// over blocks) and CBC encrypt (parallel over pages).
+//
+// All four share one structure: one CTA of 1024 threads per SM fills its
+// replicated lookup tables into shared memory once (see aes_device.cuh), then
+// every warp walks its own contiguous range of the buffer 32 blocks (512 B)
+// at a time, one 16-byte block per lane, so each warp-wide load and store is a
+// fully coalesced 512-byte transaction.  The work is split evenly over warps
+// with the warp index interleaved across CTAs, so every SM gets the same share.
+#include <cuda_runtime.h>
+
+#include "aes_device.cuh"
+#include "kgpu_internal.h"
+
+namespace kgpu {
+
+using namespace dev;
+
+static_assert(kSmemBase == (uint32_t)kSmemReservedBytes, "table offsets assume the reserved shared area");
+
+// Cipher constants, uploaded once per device by upload_tables().
+__device__ uint32_t g_te0[256];
+__device__ uint32_t g_td0[256];
+__device__ uint32_t g_isb4[256];
+
+namespace {
+
+// Regions A/B <- T0..T3 built from base[] by byte rotation.
+__device__ __forceinline__ void fill_round_tables(uint32_t* w, const uint32_t* base) {
+    for (uint32_t i = threadIdx.x; i < 2 * 16384; i += blockDim.x) {
+        uint32_t x = (i >> 6) & 255u;
+        uint32_t k = ((i >> 14) << 1) | ((i >> 5) & 1u);
+        uint32_t v = base[x];
+        w[i] = __funnelshift_l(v, v, 8 * k);
+    }
+}
+
+__device__ __forceinline__ void fill_enc(char* smem) {
+    fill_round_tables(reinterpret_cast<uint32_t*>(smem), g_te0);
+}
+
+// Regions A/B <- Td0..Td3; region C <- InvS (first half) | Te0 (second half).
+__device__ __forceinline__ void fill_dec(char* smem) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(smem);
+    fill_round_tables(w, g_td0);
+    for (uint32_t i = threadIdx.x; i < 16384; i += blockDim.x) {
+        uint32_t x = (i >> 6) & 255u;
+        w[32768 + i] = (i & 32u) ? g_te0[x] : g_isb4[x];
+    }
+}
+
+__device__ __forceinline__ void xor4(uint4& v, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    v.x ^= a;
+    v.y ^= b;
+    v.z ^= c;
+    v.w ^= d;
+}
+
+// Even split of n items over the warps of the grid: [begin, end) for this warp.
+__device__ __forceinline__ void warp_range(uint64_t n, uint64_t& begin, uint64_t& end) {
+    const uint64_t W = total_warps(), wg = interleaved_warp();
+    begin = n * wg / W;
+    end = n * (wg + 1) / W;
+}
+
+// ---------------------------------------------------------------------------
+// XTS (and ECB when TWEAK is false).
+//
+// Tweaks: a warp keeps E_K2 of 32 consecutive data units in its lanes (lane i
+// holds the unit `base + i`, one AES per lane, computed together).  A lane
+// moving to block j of a new unit takes that unit's E_K2 by shuffle and
+// multiplies by alpha^j in closed form (j < 32 there); a lane staying in its
+// unit steps its tweak by alpha^32.  So the tweak costs one extra AES per
+// data unit and a few shifts per block -- never a sequential chain.
+// ---------------------------------------------------------------------------
+template <int NR, int DIR, bool TWEAK>
+__global__ void __launch_bounds__(kBulkThreads, 1) bulk_kernel(const __grid_constant__ BulkParams p) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;  // uniform over the CTA; refused at init
+    if (DIR == 0) fill_enc(smem);
+    else fill_dec(smem);
+    __syncthreads();
+
+    const uint32_t lane = lane_id();
+    const Rep4 T{lane * 4u, lane * 4u + 128u};
+    const Rep1<2> IS{lane * 4u};
+    const Rep1<2> TE{lane * 4u + 128u};
+    const ParamKey K{p.rk};
+    const ParamKey TK{p.tk};
+
+    uint64_t c0, c1;
+    warp_range((p.nblocks + 31) >> 5, c0, c1);
+    if (c0 >= c1) return;
+
+    uint64_t blk = (c0 << 5) + lane;
+    const uint32_t bps = p.bps;
+    uint64_t base = 0;
+    uint32_t srel = 0, j = 0;
+    uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0;  // E_K2(unit base + lane)
+    uint32_t t0 = 0, t1 = 0, t2 = 0, t3 = 0;  // tweak of this lane's block
+
+    auto tweak_batch = [&]() {
+        uint64_t unit = p.first_sector + base + lane;
+        z0 = (uint32_t)unit;
+        z1 = (uint32_t)(unit >> 32);
+        z2 = 0;
+        z3 = 0;
+        if (DIR == 0) encrypt_block<NR>(z0, z1, z2, z3, T, TK);
+        else encrypt_block<NR>(z0, z1, z2, z3, TE, TK);
+    };
+
+    if (TWEAK) {
+        base = (c0 << 5) / bps;
+        uint64_t sabs = blk / bps;
+        srel = (uint32_t)(sabs - base);
+        j = (uint32_t)(blk - sabs * bps);
+        tweak_batch();
+        t0 = __shfl_sync(0xffffffffu, z0, srel);
+        t1 = __shfl_sync(0xffffffffu, z1, srel);
+        t2 = __shfl_sync(0xffffffffu, z2, srel);
+        t3 = __shfl_sync(0xffffffffu, z3, srel);
+        gf128_mul_xpow(t0, t1, t2, t3, j);
+    }
+
+    for (uint64_t c = c0; c < c1; ++c) {
+        const bool valid = blk < p.nblocks;
+        uint4 v = valid ? p.src[blk] : make_uint4(0, 0, 0, 0);
+        if (TWEAK) xor4(v, t0, t1, t2, t3);
+        if (DIR == 0) encrypt_block<NR>(v.x, v.y, v.z, v.w, T, K);
+        else decrypt_block<NR>(v.x, v.y, v.z, v.w, T, IS, K);
+        if (TWEAK) xor4(v, t0, t1, t2, t3);
+        if (valid) p.dst[blk] = v;
+        blk += 32;
+
+        if (TWEAK && c + 1 < c1) {
+            j += 32;
+            bool crossed = false;
+            if (j >= bps) {
+                uint32_t ns = j / bps;
+                srel += ns;
+                j -= ns * bps;
+                crossed = true;
+            }
+            if (__any_sync(0xffffffffu, srel >= 32)) {
+                uint32_t adv = __shfl_sync(0xffffffffu, srel, 0);
+                base += adv;
+                srel -= adv;
+                tweak_batch();
+            }
+            if (__any_sync(0xffffffffu, crossed)) {
+                uint32_t u0 = __shfl_sync(0xffffffffu, z0, srel & 31);
+                uint32_t u1 = __shfl_sync(0xffffffffu, z1, srel & 31);
+                uint32_t u2 = __shfl_sync(0xffffffffu, z2, srel & 31);
+                uint32_t u3 = __shfl_sync(0xffffffffu, z3, srel & 31);
+                if (crossed) {
+                    t0 = u0;
+                    t1 = u1;
+                    t2 = u2;
+                    t3 = u3;
+                    gf128_mul_xk(t0, t1, t2, t3, j);
+                }
+            }
+            if (!crossed) gf128_mul_x32(t0, t1, t2, t3);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CBC decryption, one block per lane.  P_i = D(C_i) ^ C_{i-1}: C_{i-1} comes
+// from the neighbouring lane by shuffle (lane 0 takes lane 31's block of the
+// previous step), and from the page IV at the first block of a page.  Warps
+// own whole pages and every block is read and written by the same lane, so
+// in-place decryption needs no synchronisation.
+// ---------------------------------------------------------------------------
+template <int NR>
+__global__ void __launch_bounds__(kBulkThreads, 1) cbc_dec_kernel(const __grid_constant__ CbcParams p) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;
+    fill_dec(smem);
+    __syncthreads();
+
+    const uint32_t lane = lane_id();
+    const Rep4 T{lane * 4u, lane * 4u + 128u};
+    const Rep1<2> IS{lane * 4u};
+    const ParamKey K{p.rk};
+
+    uint64_t u0, u1;
+    warp_range(p.npages, u0, u1);
+    if (u0 >= u1) return;
+
+    const uint32_t bpp = p.bpp;
+    const uint64_t bend = u1 * bpp;
+    uint64_t blk = u0 * bpp + lane;
+    uint64_t page = u0 + lane / bpp;
+    uint32_t j = lane % bpp;
+    uint4 carry = make_uint4(0, 0, 0, 0);
+
+    for (uint64_t b = u0 * bpp; b < bend; b += 32) {
+        const bool valid = blk < bend;
+        const uint4 c = valid ? p.src[blk] : make_uint4(0, 0, 0, 0);
+        uint4 prev;
+        prev.x = __shfl_up_sync(0xffffffffu, c.x, 1);
+        prev.y = __shfl_up_sync(0xffffffffu, c.y, 1);
+        prev.z = __shfl_up_sync(0xffffffffu, c.z, 1);
+        prev.w = __shfl_up_sync(0xffffffffu, c.w, 1);
+        if (lane == 0) prev = carry;
+        if (valid && j == 0) prev = p.ivs[page];
+        carry.x = __shfl_sync(0xffffffffu, c.x, 31);
+        carry.y = __shfl_sync(0xffffffffu, c.y, 31);
+        carry.z = __shfl_sync(0xffffffffu, c.z, 31);
+        carry.w = __shfl_sync(0xffffffffu, c.w, 31);
+        uint4 v = c;
+        decrypt_block<NR>(v.x, v.y, v.z, v.w, T, IS, K);
+        xor4(v, prev.x, prev.y, prev.z, prev.w);
+        if (valid) p.dst[blk] = v;
+        blk += 32;
+        j += 32;
+        if (j >= bpp) {
+            uint32_t ns = j / bpp;
+            page += ns;
+            j -= ns * bpp;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CBC encryption, one page per lane: C_i = E(P_i ^ C_{i-1}) is a sequential
+// chain inside a page, so parallelism comes from pages.  Warps take groups of
+// 32 pages; the next plaintext block is fetched while the current one is
+// encrypted.
+// ---------------------------------------------------------------------------
+template <int NR>
+__global__ void __launch_bounds__(kBulkThreads, 1) cbc_enc_kernel(const __grid_constant__ CbcParams p) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;
+    fill_enc(smem);
+    __syncthreads();
+
+    const uint32_t lane = lane_id();
+    const Rep4 T{lane * 4u, lane * 4u + 128u};
+    const ParamKey K{p.rk};
+    const uint32_t bpp = p.bpp;
+    const uint64_t ngroups = (p.npages + 31) >> 5;
+
+    for (uint64_t g = interleaved_warp(); g < ngroups; g += total_warps()) {
+        const uint64_t page = (g << 5) + lane;
+        if (page >= p.npages) continue;  // no shuffles below: divergence is fine
+        const uint4* in = p.src + page * bpp;
+        uint4* out = p.dst + page * bpp;
+        uint4 x = p.ivs[page];
+        uint4 nxt = in[0];
+        for (uint32_t i = 0; i < bpp; ++i) {
+            const uint4 cur = nxt;
+            if (i + 1 < bpp) nxt = in[i + 1];
+            xor4(x, cur.x, cur.y, cur.z, cur.w);
+            encrypt_block<NR>(x.x, x.y, x.z, x.w, T, K);
+            out[i] = x;
+        }
+    }
+}
+
+template <class P>
+using KernelFn = void (*)(P);
+
+inline int grid_for(uint64_t warp_items, int num_sms) {
+    // warp_items: how many warp-sized work items exist; at least one per warp.
+    uint64_t ctas = (warp_items + (kBulkThreads / 32) - 1) / (kBulkThreads / 32);
+    if (ctas < 1) ctas = 1;
+    if (ctas > (uint64_t)num_sms) ctas = num_sms;
+    return (int)ctas;
+}
+
+template <int NR>
+KernelFn<BulkParams> pick_bulk(int dir, bool tweak) {
+    if (tweak) return dir == 0 ? bulk_kernel<NR, 0, true> : bulk_kernel<NR, 1, true>;
+    return dir == 0 ? bulk_kernel<NR, 0, false> : bulk_kernel<NR, 1, false>;
+}
+
+KernelFn<BulkParams> bulk_fn(int nr, int dir, bool tweak) {
+    switch (nr) {
+        case 10: return pick_bulk<10>(dir, tweak);
+        case 12: return pick_bulk<12>(dir, tweak);
+        case 14: return pick_bulk<14>(dir, tweak);
+        default: return nullptr;
+    }
+}
+
+KernelFn<CbcParams> cbc_fn(int nr, bool enc) {
+    switch (nr) {
+        case 10: return enc ? cbc_enc_kernel<10> : cbc_dec_kernel<10>;
+        case 12: return enc ? cbc_enc_kernel<12> : cbc_dec_kernel<12>;
+        case 14: return enc ? cbc_enc_kernel<14> : cbc_dec_kernel<14>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+cudaError_t configure_kernels() {
+    for (int nr : {10, 12, 14}) {
+        for (int dir = 0; dir < 2; dir++) {
+            for (bool tw : {false, true}) {
+                cudaError_t e = cudaFuncSetAttribute(bulk_fn(nr, dir, tw), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)(dir == 0 ? kSmemEnc : kSmemDec));
+                if (e != cudaSuccess) return e;
+            }
+        }
+        cudaError_t e = cudaFuncSetAttribute(cbc_fn(nr, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemEnc);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(cbc_fn(nr, false), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDec);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t upload_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* isb4) {
+    cudaError_t e = cudaMemcpyToSymbol(g_te0, te0, 1024);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_td0, td0, 1024);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_isb4, isb4, 1024);
+    return e;
+}
+
+static cudaError_t launch_bulk(const BulkParams& p, int nr, int dir, bool tweak, int num_sms, cudaStream_t s) {
+    auto fn = bulk_fn(nr, dir, tweak);
+    if (!fn) return cudaErrorInvalidValue;
+    int grid = grid_for((p.nblocks + 31) / 32, num_sms);
+    fn<<<grid, kBulkThreads, dir == 0 ? kSmemEnc : kSmemDec, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xts(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s) {
+    return launch_bulk(p, nr, dir, true, num_sms, s);
+}
+
+cudaError_t launch_ecb(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s) {
+    return launch_bulk(p, nr, dir, false, num_sms, s);
+}
+
+cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
+    auto fn = cbc_fn(nr, false);
+    if (!fn) return cudaErrorInvalidValue;
+    int grid = grid_for(p.npages, num_sms);
+    fn<<<grid, kBulkThreads, kSmemDec, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
+    auto fn = cbc_fn(nr, true);
+    if (!fn) return cudaErrorInvalidValue;
+    int grid = grid_for((p.npages + 31) / 32, num_sms);
+    fn<<<grid, kBulkThreads, kSmemEnc, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace kgpu

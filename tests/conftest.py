@@ -19,3 +19,25 @@ def kgpu_lib():
     import paper_1305_3345_gb300 as kg
     kg.ensure_built()
     return kg
+
+
+@pytest.fixture(scope="session")
+def ctx(kgpu_lib):
+    """One library context on cuda:0 for the GPU tests."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = kgpu_lib.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def to_dev(a):
+    """numpy uint8 -> CUDA uint8 tensor (copy)."""
+    import torch
+    return torch.from_numpy(a.copy()).cuda()
+
+
+def to_np(t):
+    return t.cpu().numpy()
