@@ -162,6 +162,81 @@ int kgpu_aes_ecb_crypt(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, vo
 int kgpu_aes_xts_crypt_host(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,
                             size_t du_size, uint64_t first_sector, size_t chunk_bytes);
 
+/* ------------------------------------------------------------------------
+ * Batched submission: the paper's service-request protocol (section 3.2:
+ * build a request, place it in the request queue, then wait by blocking or
+ * by busy-waiting on the response queue), with many requests per submission.
+ * ---------------------------------------------------------------------- */
+
+/* One request of a batch.  All pointers are DEVICE pointers. */
+typedef struct kgpu_request {
+    uint32_t mode;       /* KGPU_MODE_* */
+    uint32_t dir;        /* KGPU_ENCRYPT / KGPU_DECRYPT for XTS and ECB; ignored for CBC */
+    kgpu_key key;        /* an XTS key for KGPU_MODE_XTS, a single key otherwise */
+    uint32_t flags;      /* must be 0 */
+    const void *src;     /* 16-byte aligned */
+    void *dst;           /* == src (in place) or disjoint from it */
+    uint64_t len;        /* bytes: a multiple of unit_size (ECB: of 16) */
+    uint64_t unit_size;  /* XTS data-unit size / CBC page size; ignored for ECB */
+    uint64_t sector;     /* XTS: number of the first data unit */
+    const uint8_t *ivs;  /* CBC: len / unit_size IVs of 16 bytes, not overlapping dst */
+} kgpu_request;
+
+/* Launch shape of the persistent batch kernel (see kgpu_autotune). */
+typedef struct kgpu_tuning {
+    uint32_t threads;      /* threads per CTA: 256 or 512 (default 512) */
+    uint32_t tile_chunks;  /* work per XTS/ECB tile in 512-byte chunks (default 32 = 16 KiB);
+                              CBC-decrypt tiles hold the same bytes in whole pages,
+                              CBC-encrypt tiles hold up to 32 pages (one chain per lane) */
+    uint32_t ctas;         /* CTAs of the persistent kernel (default 0 = one per SM) */
+    uint32_t reserved;
+} kgpu_tuning;
+
+/*
+ * Submit n requests as ONE launch of a persistent kernel on `stream`: warps
+ * pull fixed-size tiles of the requests from a shared counter, whatever their
+ * mode, key or size.  The requests are validated first; if any is malformed
+ * nothing is launched, KGPU_EINVAL/KGPU_ENOENT/KGPU_EFAULT is returned and,
+ * when req_status is non-NULL, req_status[i] holds each request's own code.
+ * The descriptors are copied into one of four rotating pinned staging slots
+ * (the paper's four static pinned buffers, section 3.2) and the submission is
+ * replayed as a CUDA graph {copy in, clear, kernel, copy status out}.  When
+ * all four slots hold unfinished batches, submit blocks until the oldest ends.
+ * *out receives a ticket for kgpu_poll.  n == 0 gives a ticket that is
+ * already complete.  Requests of one batch run concurrently and in no fixed
+ * order: no request may write bytes that another request of the same batch
+ * reads or writes.
+ */
+int kgpu_submit(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream stream, kgpu_ticket *out,
+                int *req_status);
+
+/*
+ * Wait for a ticket (the response queue).  timeout_ns == 0: check once
+ * (busy-wait by calling again); < 0: block until complete; > 0: wait at most
+ * that long.  Returns KGPU_OK when the batch is complete (req_status, if not
+ * NULL, receives each request's status: 0, or KGPU_ENOENT if its key was
+ * deleted before it ran), KGPU_ETIMEDOUT if it is still running, and
+ * KGPU_ENOENT for an unknown ticket or one whose slot has since been reused
+ * by a later submission.
+ */
+int kgpu_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *req_status);
+
+/* Set / read the batch kernel's launch shape (validated: KGPU_EINVAL). */
+int kgpu_set_tuning(kgpu_ctx *ctx, const kgpu_tuning *t);
+int kgpu_get_tuning(kgpu_ctx *ctx, kgpu_tuning *t);
+
+/*
+ * Autotuner: runs the given batch (iters timed repetitions per candidate,
+ * after one warm-up) under each candidate launch shape -- threads per CTA x
+ * tile size -- times each with CUDA events on `stream`, keeps the fastest in
+ * the context and returns it in *best (and its mean time in *best_ms if not
+ * NULL).  The batch is executed many times, so every request must be out of
+ * place (src != dst); in-place requests are rejected with KGPU_EINVAL.
+ * Blocks until done.
+ */
+int kgpu_autotune(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream stream, uint32_t iters,
+                  kgpu_tuning *best, float *best_ms);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

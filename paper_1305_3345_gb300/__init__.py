@@ -39,6 +39,38 @@ class KgpuError(RuntimeError):
         super().__init__(f"{what} failed: {self.code} ({rc})")
 
 
+class KgpuRequest(ctypes.Structure):
+    """kgpu_request (include/kgpu.h)."""
+    _fields_ = [("mode", ctypes.c_uint32), ("dir", ctypes.c_uint32), ("key", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("src", ctypes.c_void_p), ("dst", ctypes.c_void_p),
+                ("len", ctypes.c_uint64), ("unit_size", ctypes.c_uint64), ("sector", ctypes.c_uint64),
+                ("ivs", ctypes.c_void_p)]
+
+
+class KgpuTuning(ctypes.Structure):
+    """kgpu_tuning (include/kgpu.h)."""
+    _fields_ = [("threads", ctypes.c_uint32), ("tile_chunks", ctypes.c_uint32), ("ctas", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"threads": self.threads, "tile_chunks": self.tile_chunks, "ctas": self.ctas}
+
+
+# numpy view of an array of kgpu_request, for building large batches cheaply
+REQUEST_DTYPE = None
+
+
+def request_dtype():
+    global REQUEST_DTYPE
+    if REQUEST_DTYPE is None:
+        import numpy as np
+        REQUEST_DTYPE = np.dtype([("mode", "<u4"), ("dir", "<u4"), ("key", "<u4"), ("flags", "<u4"),
+                                  ("src", "<u8"), ("dst", "<u8"), ("len", "<u8"), ("unit_size", "<u8"),
+                                  ("sector", "<u8"), ("ivs", "<u8")])
+        assert REQUEST_DTYPE.itemsize == ctypes.sizeof(KgpuRequest)
+    return REQUEST_DTYPE
+
+
 class KgpuConfig(ctypes.Structure):
     _fields_ = [("max_keys", ctypes.c_uint32), ("ring_slots", ctypes.c_uint32),
                 ("admit_bytes", ctypes.c_uint64), ("idle_timeout_ns", ctypes.c_uint64),
@@ -73,6 +105,12 @@ def lib() -> ctypes.CDLL:
                 "kgpu_aes_cbc_encrypt_pages": ([vp, u32, vp, vp, sz, sz, vp, vp], i32),
                 "kgpu_aes_ecb_crypt": ([vp, u32, i32, vp, vp, sz, vp], i32),
                 "kgpu_aes_xts_crypt_host": ([vp, u32, i32, vp, vp, sz, sz, u64, sz], i32),
+                "kgpu_submit": ([vp, vp, sz, vp, ctypes.POINTER(u64), vp], i32),
+                "kgpu_poll": ([vp, u64, ctypes.c_int64, vp], i32),
+                "kgpu_set_tuning": ([vp, ctypes.POINTER(KgpuTuning)], i32),
+                "kgpu_get_tuning": ([vp, ctypes.POINTER(KgpuTuning)], i32),
+                "kgpu_autotune": ([vp, vp, sz, vp, u32, ctypes.POINTER(KgpuTuning), ctypes.POINTER(ctypes.c_float)],
+                                  i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -203,6 +241,61 @@ def kgpu_aes_xts_crypt_host(ctx, key: int, dir: int, src, dst, du_size: int, fir
            "kgpu_aes_xts_crypt_host")
 
 
+def _req_array(reqs):
+    """(pointer, count, keepalive) of a batch given as a numpy array of
+    request_dtype() or a sequence of KgpuRequest."""
+    import numpy as np
+    if isinstance(reqs, np.ndarray):
+        if reqs.dtype != request_dtype() or not reqs.flags["C_CONTIGUOUS"]:
+            raise TypeError("request array must be contiguous with request_dtype()")
+        return reqs.ctypes.data, reqs.size, reqs
+    arr = (KgpuRequest * len(reqs))(*reqs)
+    return ctypes.addressof(arr), len(reqs), arr
+
+
+def kgpu_submit(ctx, reqs, stream=None, status=None) -> int:
+    """Submit a batch; returns the ticket.  status: optional int32 numpy array
+    (len n) that receives each request's validation code."""
+    ptr, n, keep = _req_array(reqs)
+    t = ctypes.c_uint64()
+    sp = status.ctypes.data if status is not None else None
+    rc = lib().kgpu_submit(ctx, ptr, n, _stream(stream), ctypes.byref(t), sp)
+    del keep
+    _check(rc, "kgpu_submit")
+    return t.value
+
+
+def kgpu_poll(ctx, ticket: int, timeout_ns: int = -1, status=None) -> int:
+    """0 when complete, KGPU_ETIMEDOUT (-110) while running; raises otherwise."""
+    sp = status.ctypes.data if status is not None else None
+    rc = lib().kgpu_poll(ctx, ticket, timeout_ns, sp)
+    if rc == -110:
+        return rc
+    return _check(rc, "kgpu_poll")
+
+
+def kgpu_set_tuning(ctx, threads=0, tile_chunks=0, ctas=0) -> None:
+    t = KgpuTuning(threads, tile_chunks, ctas, 0)
+    _check(lib().kgpu_set_tuning(ctx, ctypes.byref(t)), "kgpu_set_tuning")
+
+
+def kgpu_get_tuning(ctx) -> dict:
+    t = KgpuTuning()
+    _check(lib().kgpu_get_tuning(ctx, ctypes.byref(t)), "kgpu_get_tuning")
+    return t.as_dict()
+
+
+def kgpu_autotune(ctx, reqs, stream=None, iters: int = 3):
+    """Returns (best tuning dict, mean ms of the best)."""
+    ptr, n, keep = _req_array(reqs)
+    best = KgpuTuning()
+    ms = ctypes.c_float()
+    rc = lib().kgpu_autotune(ctx, ptr, n, _stream(stream), iters, ctypes.byref(best), ctypes.byref(ms))
+    del keep
+    _check(rc, "kgpu_autotune")
+    return best.as_dict(), ms.value
+
+
 class Context:
     """Owns one kgpu_ctx on a device; methods mirror the C ABI without the ctx."""
 
@@ -247,3 +340,18 @@ class Context:
 
     def xts_crypt_host(self, key, dir, src, dst, du_size, first_sector=0, chunk_bytes=0):
         kgpu_aes_xts_crypt_host(self.handle, key, dir, src, dst, du_size, first_sector, chunk_bytes)
+
+    def submit(self, reqs, stream=None, status=None) -> int:
+        return kgpu_submit(self.handle, reqs, stream, status)
+
+    def poll(self, ticket, timeout_ns=-1, status=None) -> int:
+        return kgpu_poll(self.handle, ticket, timeout_ns, status)
+
+    def set_tuning(self, threads=0, tile_chunks=0, ctas=0):
+        kgpu_set_tuning(self.handle, threads, tile_chunks, ctas)
+
+    def get_tuning(self) -> dict:
+        return kgpu_get_tuning(self.handle)
+
+    def autotune(self, reqs, stream=None, iters=3):
+        return kgpu_autotune(self.handle, reqs, stream, iters)

@@ -26,6 +26,7 @@ namespace kgpu {
 namespace dev {
 
 constexpr uint32_t kRegion = 65536;
+constexpr int kMaxKeyWords = 60;
 
 __device__ __forceinline__ uint32_t rotl8(uint32_t v) { return __byte_perm(v, v, 0x2103); }
 __device__ __forceinline__ uint32_t rotl16(uint32_t v) { return __byte_perm(v, v, 0x1032); }
@@ -48,11 +49,13 @@ __device__ __forceinline__ uint32_t rotl_bytes(uint32_t v) {
 constexpr uint32_t kSmemBase = 1024;
 
 // Shared address (relative to the table base) of byte P of state word s in a
-// 256-B-row replicated table, with lo = lane*4 (first half of the row) or
-// lane*4 + 128 (second half): one PRMT.
+// 256-B-row replicated table: one PRMT.  lo = lane*4 (first half of the row)
+// or lane*4 + 128 (second half) in its byte 0, byte 1 zero, and optionally a
+// region index in byte 2; the index byte lands in byte 1 and lo's bytes 0, 2
+// and 3 pass through.
 template <int P>
 __device__ __forceinline__ uint32_t row_addr(uint32_t s, uint32_t lo) {
-    return __byte_perm(s, lo, 0x5504u | (P << 4));
+    return __byte_perm(s, lo, 0x7604u | (P << 4));
 }
 
 // 32-bit shared load at table offset a + OFF (OFF includes kSmemBase and the
@@ -222,6 +225,111 @@ __device__ __forceinline__ uint32_t interleaved_warp() {
 }
 
 __device__ __forceinline__ uint32_t total_warps() { return (blockDim.x >> 5) * gridDim.x; }
+
+// ---------------------------------------------------------------------------
+// Unified two-table cipher (batched and serving kernels, which must serve any
+// mode, direction and key size from one CTA).
+//
+// Layout: region A = Te0 | Te1, region B = Td0 | Td1, region C = S4 | IS4
+// (S(x) / InvS(x) in all four bytes), each replicated per lane as above.  The
+// region index travels in byte 2 of the lane-offset registers, so one code path
+// serves both directions.  Rows 2 and 3 are rows 0 and 1 rotated by 16 bits,
+// and rotation commutes with xor, so per column
+//     T2[c] ^ T3[d] ^ k  =  rotl16(T0[c] ^ T1[d] ^ rotr16(k))
+// -- one PRMT, with rotr16(k) prepared on the host (u-frame key layout).
+// The inverse cipher is run on the state permuted to (s0, s3, s2, s1): in that
+// order InvShiftRows has exactly ShiftRows' shape, so the round code is shared.
+// ---------------------------------------------------------------------------
+
+// Lane-offset registers of the unified layout for one direction.
+struct UniLanes {
+    uint32_t r0;  // lane*4 | region << 16: row 0 table (Te0 or Td0)
+    uint32_t r1;  // r0 + 128: row 1 table (Te1 or Td1)
+    uint32_t f;   // lane*4 (+128 for InvS) | 2 << 16: final-round S-box
+};
+
+__device__ __forceinline__ UniLanes uni_lanes(uint32_t lane, int dir) {
+    uint32_t base = lane * 4u | (uint32_t)dir << 16;
+    return UniLanes{base, base + 128u, (lane * 4u + (dir ? 128u : 0u)) | (2u << 16)};
+}
+
+__device__ __forceinline__ uint32_t uni_col(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t kr,
+                                            const UniLanes& L) {
+    uint32_t hi = lds_tab<kSmemBase>(row_addr<2>(c, L.r0)) ^ lds_tab<kSmemBase>(row_addr<3>(d, L.r1)) ^ kr;
+    return lds_tab<kSmemBase>(row_addr<0>(a, L.r0)) ^ lds_tab<kSmemBase>(row_addr<1>(b, L.r1)) ^ rotl16(hi);
+}
+
+// Round keys in registers (compile-time indices after unrolling).
+struct RegKey {
+    uint32_t w_[kMaxKeyWords];
+    __device__ __forceinline__ uint32_t w(int i) const { return w_[i]; }
+    __device__ __forceinline__ void load(const uint32_t* g) {
+        const uint4* g4 = reinterpret_cast<const uint4*>(g);
+#pragma unroll
+        for (int i = 0; i < kMaxKeyWords / 4; i++) {
+            uint4 v = g4[i];
+            w_[4 * i] = v.x;
+            w_[4 * i + 1] = v.y;
+            w_[4 * i + 2] = v.z;
+            w_[4 * i + 3] = v.w;
+        }
+    }
+};
+
+// Round keys in this warp's shared-memory slot (generic pointer into shared).
+struct SmemKey {
+    const uint32_t* p;
+    __device__ __forceinline__ uint32_t w(int i) const { return p[i]; }
+};
+
+// One block through the cipher of the unified layout (u-frame state and key).
+template <class Key>
+__device__ __forceinline__ void cipher_u(uint32_t& u0, uint32_t& u1, uint32_t& u2, uint32_t& u3, const Key& k,
+                                         int nr, const UniLanes& L) {
+    u0 ^= k.w(0);
+    u1 ^= k.w(1);
+    u2 ^= k.w(2);
+    u3 ^= k.w(3);
+#pragma unroll
+    for (int r = 1; r < 14; r++) {
+        if (r < nr) {
+            uint32_t t0 = uni_col(u0, u1, u2, u3, k.w(4 * r + 0), L);
+            uint32_t t1 = uni_col(u1, u2, u3, u0, k.w(4 * r + 1), L);
+            uint32_t t2 = uni_col(u2, u3, u0, u1, k.w(4 * r + 2), L);
+            uint32_t t3 = uni_col(u3, u0, u1, u2, k.w(4 * r + 3), L);
+            u0 = t0;
+            u1 = t1;
+            u2 = t2;
+            u3 = t3;
+        }
+    }
+#define KGPU_FIN(P, x) lds_tab<kSmemBase>(row_addr<P>(x, L.f))
+    uint32_t o0 = merge_bytes(KGPU_FIN(0, u0), KGPU_FIN(1, u1), KGPU_FIN(2, u2), KGPU_FIN(3, u3)) ^ k.w(56);
+    uint32_t o1 = merge_bytes(KGPU_FIN(0, u1), KGPU_FIN(1, u2), KGPU_FIN(2, u3), KGPU_FIN(3, u0)) ^ k.w(57);
+    uint32_t o2 = merge_bytes(KGPU_FIN(0, u2), KGPU_FIN(1, u3), KGPU_FIN(2, u0), KGPU_FIN(3, u1)) ^ k.w(58);
+    uint32_t o3 = merge_bytes(KGPU_FIN(0, u3), KGPU_FIN(1, u0), KGPU_FIN(2, u1), KGPU_FIN(3, u2)) ^ k.w(59);
+#undef KGPU_FIN
+    u0 = o0;
+    u1 = o1;
+    u2 = o2;
+    u3 = o3;
+}
+
+// Block in natural column order through the unified cipher in direction dir.
+template <class Key>
+__device__ __forceinline__ void cipher_block(uint4& v, const Key& k, int nr, const UniLanes& L, int dir) {
+    if (dir) {
+        uint32_t t = v.y;
+        v.y = v.w;
+        v.w = t;
+    }
+    cipher_u(v.x, v.y, v.z, v.w, k, nr, L);
+    if (dir) {
+        uint32_t t = v.y;
+        v.y = v.w;
+        v.w = t;
+    }
+}
 
 }  // namespace dev
 }  // namespace kgpu

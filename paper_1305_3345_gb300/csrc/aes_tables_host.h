@@ -124,3 +124,28 @@ inline void decrypt_schedule(const uint32_t* enc, int nr, uint32_t* dec) {
 
 }  // namespace host
 }  // namespace kgpu
+
+namespace kgpu {
+namespace host {
+
+// Unified-kernel ("u-frame") copy of a schedule: see DevKey in
+// kgpu_internal.h.  perm_dec = true stores each round's words in the state
+// order (0, 3, 2, 1) used for the inverse cipher.
+inline void to_uframe(const uint32_t* sched, int nr, bool perm_dec, uint32_t* out) {
+    for (int i = 0; i < 60; i++) out[i] = 0;
+    for (int r = 0; r <= nr; r++) {
+        for (int c = 0; c < 4; c++) {
+            uint32_t w = sched[4 * r + (perm_dec ? (4 - c) % 4 : c)];
+            if (r == 0) {
+                out[c] = w;
+            } else if (r == nr) {
+                out[56 + c] = w;
+            } else {
+                out[4 * r + c] = (w >> 16) | (w << 16);
+            }
+        }
+    }
+}
+
+}  // namespace host
+}  // namespace kgpu

@@ -10,144 +10,11 @@
 #include <vector>
 
 #include "aes_tables_host.h"
-#include "kgpu_internal.h"
+#include "kgpu_ctx.h"
 
 using namespace kgpu;
+using namespace kgpu::hostutil;
 
-struct kgpu_ctx {
-    int device = 0;
-    int num_sms = 0;
-    kgpu_config cfg{};
-    std::mutex mu;
-    std::vector<HostKey> keys;
-    DevKey* d_keys = nullptr;
-
-    // host-resident pipeline (kgpu_aes_xts_crypt_host): three device staging
-    // buffers on three streams -- one chunk being copied in, one transformed,
-    // one copied out (the GPU-side triple buffering of the paper's section 3.2)
-    static constexpr int kStages = 3;
-    std::mutex host_mu;
-    cudaStream_t hs[kStages] = {};
-    uint8_t* staging[kStages] = {};
-    size_t staging_bytes = 0;
-};
-
-namespace {
-
-constexpr int kVersion = (0 << 16) | 3;
-
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev_);
-        if (prev_ != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (cur != prev_) cudaSetDevice(prev_);
-    }
-
-  private:
-    int prev_ = 0;
-};
-
-int from_cuda(cudaError_t e) {
-    if (e == cudaSuccess) return KGPU_OK;
-    if (e == cudaErrorMemoryAllocation) return KGPU_ENOMEM;
-    return KGPU_EIO;
-}
-
-// cuMemGetAddressRange through the runtime's driver entry-point table, so the
-// library has no link-time dependency on libcuda (it loads on GPU-less hosts).
-typedef CUresult (*AddressRangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
-
-AddressRangeFn address_range_fn() {
-    static AddressRangeFn fn = []() -> AddressRangeFn {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        return reinterpret_cast<AddressRangeFn>(f);
-    }();
-    return fn;
-}
-
-// [p, p + len) must be device (or managed) memory of ctx's device, inside one
-// allocation.
-int check_device_range(const kgpu_ctx* ctx, const void* p, size_t len) {
-    if (!p) return KGPU_EFAULT;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return KGPU_EFAULT;
-    }
-    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return KGPU_EFAULT;
-    if (a.type == cudaMemoryTypeDevice && a.device != ctx->device) return KGPU_EFAULT;
-    CUdeviceptr base = 0;
-    size_t size = 0;
-    AddressRangeFn range = address_range_fn();
-    if (!range || range(&base, &size, (CUdeviceptr)p) != CUDA_SUCCESS) return KGPU_EFAULT;
-    uintptr_t end = (uintptr_t)p + len;
-    if (end < (uintptr_t)p || end > (uintptr_t)base + size) return KGPU_EFAULT;
-    return KGPU_OK;
-}
-
-int check_host_ptr(const void* p) {
-    if (!p) return KGPU_EFAULT;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return KGPU_EFAULT;
-    }
-    if (a.type == cudaMemoryTypeDevice) return KGPU_EFAULT;
-    return KGPU_OK;
-}
-
-// src == dst, or disjoint; 16-byte aligned.
-int check_pair(const void* src, const void* dst, size_t len) {
-    uintptr_t s = (uintptr_t)src, d = (uintptr_t)dst;
-    if ((s | d) & 15) return KGPU_EINVAL;
-    if (s != d && s < d + len && d < s + len) return KGPU_EINVAL;
-    return KGPU_OK;
-}
-
-int get_key(kgpu_ctx* ctx, kgpu_key h, bool want_xts, HostKey* out) {
-    std::lock_guard<std::mutex> g(ctx->mu);
-    if (h == 0 || h > ctx->keys.size()) return KGPU_ENOENT;
-    const HostKey& k = ctx->keys[h - 1];
-    if (!k.live || k.xts != want_xts) return KGPU_ENOENT;
-    *out = k;
-    return KGPU_OK;
-}
-
-int xts_args(kgpu_ctx* ctx, int dir, size_t len, size_t du, uint64_t first_sector) {
-    if (!ctx) return KGPU_EINVAL;
-    if (dir != KGPU_ENCRYPT && dir != KGPU_DECRYPT) return KGPU_EINVAL;
-    if (du == 0 || du % 16 || len % du) return KGPU_EINVAL;
-    if (du / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
-    uint64_t units = len / du;
-    if (units && first_sector + (units - 1) < first_sector) return KGPU_EINVAL;  // 64-bit unit numbers
-    return KGPU_OK;
-}
-
-void fill_bulk(BulkParams* p, const HostKey& k, int dir, const void* src, void* dst, size_t len, size_t du,
-               uint64_t first_sector) {
-    std::memset(p, 0, sizeof(*p));
-    p->src = static_cast<const uint4*>(src);
-    p->dst = static_cast<uint4*>(dst);
-    p->nblocks = len / 16;
-    p->bps = (uint32_t)(du / 16);
-    p->first_sector = first_sector;
-    std::memcpy(p->rk, dir == KGPU_ENCRYPT ? k.enc : k.dec, sizeof(p->rk));
-    std::memcpy(p->tk, k.twk, sizeof(p->tk));
-}
-
-}  // namespace
 
 extern "C" {
 
@@ -201,7 +68,9 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
     host::Tables t;
     host::make_tables(&t);
     int rc = from_cuda(configure_kernels());
+    if (rc == KGPU_OK) rc = from_cuda(configure_batch_kernels());
     if (rc == KGPU_OK) rc = from_cuda(upload_tables(t.te0, t.td0, t.isb4));
+    if (rc == KGPU_OK) rc = from_cuda(upload_unified_tables(t.te0, t.td0, t.sb4, t.isb4));
     if (rc == KGPU_OK) rc = from_cuda(cudaMalloc(&ctx->d_keys, sizeof(DevKey) * ctx->cfg.max_keys));
     if (rc == KGPU_OK) rc = from_cuda(cudaMemset(ctx->d_keys, 0, sizeof(DevKey) * ctx->cfg.max_keys));
     if (rc != KGPU_OK) {
@@ -225,6 +94,7 @@ int kgpu_destroy(kgpu_ctx* ctx) {
             }
             if (ctx->staging[i]) cudaFree(ctx->staging[i]);
         }
+        destroy_batch_slots(ctx);
         if (ctx->d_keys) cudaFree(ctx->d_keys);
     }
     delete ctx;
@@ -253,11 +123,11 @@ int kgpu_aes_setkey(kgpu_ctx* ctx, const uint8_t* key, size_t key_len, int xts, 
 
     DevKey dk;
     std::memset(&dk, 0, sizeof(dk));
-    std::memcpy(dk.enc, hk.enc, sizeof(dk.enc));
-    std::memcpy(dk.dec, hk.dec, sizeof(dk.dec));
-    std::memcpy(dk.twk, hk.twk, sizeof(dk.twk));
+    host::to_uframe(hk.enc, hk.nr, false, dk.encu);
+    host::to_uframe(hk.dec, hk.nr, true, dk.decu);
+    if (hk.xts) host::to_uframe(hk.twk, hk.nr, false, dk.twku);
     dk.nr = (uint32_t)hk.nr;
-    dk.flags = (hk.xts ? 1u : 0u) | 2u;
+    dk.flags = kKeyLive | (hk.xts ? kKeyXts : 0u);
 
     std::lock_guard<std::mutex> lk(ctx->mu);
     size_t slot = ctx->keys.size();

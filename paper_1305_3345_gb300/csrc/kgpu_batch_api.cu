@@ -1,0 +1,438 @@
+// Batched submission (kgpu_submit / kgpu_poll), launch-shape tuning and the
+// autotuner.  Requests are validated and packed on the host; everything they
+// ask for is computed by the persistent kernel in kgpu_unified.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "kgpu_ctx.h"
+
+using namespace kgpu;
+using namespace kgpu::hostutil;
+
+namespace {
+
+// Validated allocation ranges, built afresh for every call so that a range is
+// never trusted after the caller could have freed it.
+struct RangeCache {
+    std::vector<std::pair<uintptr_t, uintptr_t>> r;
+    int check(const kgpu_ctx* ctx, const void* p, size_t len) {
+        uintptr_t a = (uintptr_t)p, e = a + len;
+        if (!p || e < a) return KGPU_EFAULT;
+        for (auto& x : r)
+            if (a >= x.first && e <= x.second) return KGPU_OK;
+        uintptr_t base = 0;
+        size_t size = 0;
+        int rc = device_allocation(ctx, p, &base, &size);
+        if (rc) return rc;
+        r.emplace_back(base, base + size);
+        return e <= base + size ? KGPU_OK : KGPU_EFAULT;
+    }
+};
+
+kgpu_tuning default_tuning(const kgpu_ctx* ctx) {
+    kgpu_tuning t{};
+    t.threads = 512;
+    t.tile_chunks = 32;
+    t.ctas = (uint32_t)ctx->num_sms;
+    return t;
+}
+
+kgpu_tuning effective(const kgpu_ctx* ctx) {
+    kgpu_tuning t = ctx->tune;
+    kgpu_tuning d = default_tuning(ctx);
+    if (!t.threads) t.threads = d.threads;
+    if (!t.tile_chunks) t.tile_chunks = d.tile_chunks;
+    if (!t.ctas) t.ctas = d.ctas;
+    return t;
+}
+
+int tuning_ok(const kgpu_tuning* t) {
+    if (t->threads && t->threads != 256 && t->threads != 512) return KGPU_EINVAL;
+    if (t->tile_chunks > (1u << 20)) return KGPU_EINVAL;
+    if (t->ctas > 4096) return KGPU_EINVAL;
+    return KGPU_OK;
+}
+
+// Validate one request and write its device descriptor.
+int make_desc(kgpu_ctx* ctx, const kgpu_request& q, RangeCache& rc, uint32_t tile_chunks, ReqDesc* d) {
+    std::memset(d, 0, sizeof(*d));
+    if (q.flags) return KGPU_EINVAL;
+    const bool cbc = q.mode == KGPU_MODE_CBC_DEC || q.mode == KGPU_MODE_CBC_ENC;
+    const bool xts = q.mode == KGPU_MODE_XTS;
+    if (!xts && !cbc && q.mode != KGPU_MODE_ECB) return KGPU_EINVAL;
+    if ((xts || q.mode == KGPU_MODE_ECB) && q.dir != KGPU_ENCRYPT && q.dir != KGPU_DECRYPT) return KGPU_EINVAL;
+    uint64_t unit = q.mode == KGPU_MODE_ECB ? 16 : q.unit_size;
+    if (unit == 0 || unit % 16 || q.len % unit || unit / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
+    if (xts) {
+        uint64_t units = q.len / unit;
+        if (units && q.sector + (units - 1) < q.sector) return KGPU_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        if (q.key == 0 || q.key > ctx->keys.size()) return KGPU_ENOENT;
+        const HostKey& k = ctx->keys[q.key - 1];
+        if (!k.live || k.xts != xts) return KGPU_ENOENT;
+    }
+    if (q.len) {
+        int r = check_pair(q.src, q.dst, q.len);
+        if (r) return r;
+        if ((r = rc.check(ctx, q.src, q.len)) || (r = rc.check(ctx, q.dst, q.len))) return r;
+        if (cbc) {
+            uint64_t npages = q.len / unit;
+            if ((uintptr_t)q.ivs & 15) return KGPU_EINVAL;
+            if ((r = rc.check(ctx, q.ivs, npages * 16))) return r;
+            uintptr_t iv0 = (uintptr_t)q.ivs, iv1 = iv0 + npages * 16, d0 = (uintptr_t)q.dst;
+            if (iv0 < d0 + q.len && d0 < iv1) return KGPU_EINVAL;
+        }
+    }
+    d->src = static_cast<const uint4*>(q.src);
+    d->dst = static_cast<uint4*>(q.dst);
+    d->ivs = reinterpret_cast<const uint4*>(q.ivs);
+    d->nblocks = q.len / 16;
+    d->first_sector = q.sector;
+    d->unit_blocks = (uint32_t)(unit / 16);
+    d->key = q.key - 1;
+    d->mode = q.mode;
+    d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : q.dir;
+    if (q.mode == KGPU_MODE_CBC_ENC) {
+        d->tile_units = 32;  // one chain per lane
+    } else if (q.mode == KGPU_MODE_CBC_DEC) {
+        uint64_t ppt = (uint64_t)tile_chunks * 32 / d->unit_blocks;
+        d->tile_units = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ppt, 1u << 30));
+    } else {
+        d->tile_units = std::max<uint32_t>(1, tile_chunks);
+    }
+    return KGPU_OK;
+}
+
+// Validate all requests and pack header | descriptors | tile prefix into buf
+// (which must hold batch_bytes(n)).  Returns the first error, with every
+// request's own code in req_status when given.
+int pack_batch(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, uint32_t tile_chunks, uint8_t* buf,
+               int* req_status) {
+    RangeCache rc;
+    int first = KGPU_OK;
+    ReqDesc* descs = reinterpret_cast<ReqDesc*>(buf + batch_desc_offset());
+    uint64_t* prefix = reinterpret_cast<uint64_t*>(buf + batch_prefix_offset((uint32_t)n));
+    uint64_t tiles = 0;
+    for (size_t i = 0; i < n; i++) {
+        int r = make_desc(ctx, reqs[i], rc, tile_chunks, &descs[i]);
+        if (req_status) req_status[i] = r;
+        if (r && !first) first = r;
+        prefix[i] = tiles;
+        if (!r) {
+            uint64_t units = request_units(descs[i]);
+            tiles += (units + descs[i].tile_units - 1) / descs[i].tile_units;
+        }
+    }
+    prefix[n] = tiles;
+    BatchHeader* h = reinterpret_cast<BatchHeader*>(buf);
+    h->total_tiles = tiles;
+    h->nreq = (uint32_t)n;
+    h->pad = 0;
+    return first;
+}
+
+void free_slot(kgpu::BatchSlot& s) {
+    if (s.done) cudaEventSynchronize(s.done);
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    if (s.h_buf) cudaFreeHost(s.h_buf);
+    if (s.d_buf) cudaFree(s.d_buf);
+    if (s.h_status) cudaFreeHost(s.h_status);
+    if (s.d_status) cudaFree(s.d_status);
+    if (s.d_counter) cudaFree(s.d_counter);
+    if (s.done) cudaEventDestroy(s.done);
+    uint64_t gen = s.gen;
+    s = kgpu::BatchSlot();
+    s.gen = gen;
+}
+
+// Grow the slot's buffers to hold n requests and (re)build its graph when the
+// buffers or the launch shape changed.
+int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning& t) {
+    size_t need = batch_bytes((uint32_t)n);
+    bool rebuild = !s.exec || s.graph_threads != (int)t.threads || s.graph_grid != (int)t.ctas;
+    if (!s.done && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) return KGPU_EIO;
+    if (!s.d_counter && cudaMalloc(&s.d_counter, 16) != cudaSuccess) return KGPU_ENOMEM;
+    if (s.cap < need || s.status_cap < n) {
+        size_t cap = std::max(need, s.cap * 2);
+        size_t scap = std::max(n, s.status_cap * 2);
+        if (s.exec) cudaGraphExecDestroy(s.exec);
+        if (s.graph) cudaGraphDestroy(s.graph);
+        s.exec = nullptr;
+        s.graph = nullptr;
+        if (s.h_buf) cudaFreeHost(s.h_buf);
+        if (s.d_buf) cudaFree(s.d_buf);
+        if (s.h_status) cudaFreeHost(s.h_status);
+        if (s.d_status) cudaFree(s.d_status);
+        s.h_buf = nullptr;
+        s.d_buf = nullptr;
+        s.h_status = nullptr;
+        s.d_status = nullptr;
+        s.cap = s.status_cap = 0;
+        if (cudaHostAlloc(&s.h_buf, cap, cudaHostAllocDefault) != cudaSuccess ||
+            cudaMalloc(&s.d_buf, cap) != cudaSuccess ||
+            cudaHostAlloc(&s.h_status, scap * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+            cudaMalloc(&s.d_status, scap * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return KGPU_ENOMEM;
+        }
+        s.cap = cap;
+        s.status_cap = scap;
+        rebuild = true;
+    }
+    if (!rebuild) return KGPU_OK;
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.graph) cudaGraphDestroy(s.graph);
+    s.exec = nullptr;
+    s.graph = nullptr;
+
+    s.args = BatchArgs{};
+    s.args.buf = s.d_buf;
+    s.args.keys = ctx->d_keys;
+    s.args.max_keys = ctx->cfg.max_keys;
+    s.args.next_tile = s.d_counter;
+    s.args.status = s.d_status;
+
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return KGPU_EIO;
+    cudaGraphNode_t n_ctr = nullptr;
+    bool ok = cudaGraphAddMemcpyNode1D(&s.n_copy, g, nullptr, 0, s.d_buf, s.h_buf, s.cap,
+                                       cudaMemcpyHostToDevice) == cudaSuccess;
+    cudaMemsetParams mp{};
+    mp.dst = s.d_counter;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = 2;
+    mp.height = 1;
+    ok = ok && cudaGraphAddMemsetNode(&n_ctr, g, nullptr, 0, &mp) == cudaSuccess;
+    mp.dst = s.d_status;
+    mp.width = s.status_cap;
+    ok = ok && cudaGraphAddMemsetNode(&s.n_status_clear, g, nullptr, 0, &mp) == cudaSuccess;
+    cudaKernelNodeParams kp{};
+    void* kargs[] = {&s.args};
+    kp.func = const_cast<void*>(batch_kernel_fn((int)t.threads));
+    kp.gridDim = dim3(t.ctas);
+    kp.blockDim = dim3(t.threads);
+    kp.sharedMemBytes = (unsigned)unified_smem_bytes((int)t.threads);
+    kp.kernelParams = kargs;
+    cudaGraphNode_t deps[3] = {s.n_copy, n_ctr, s.n_status_clear};
+    ok = ok && kp.func && cudaGraphAddKernelNode(&s.n_kernel, g, deps, 3, &kp) == cudaSuccess;
+    ok = ok && cudaGraphAddMemcpyNode1D(&s.n_status_out, g, &s.n_kernel, 1, s.h_status, s.d_status,
+                                        s.status_cap * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaGraphInstantiate(&s.exec, g, 0) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        s.exec = nullptr;
+        return KGPU_EIO;
+    }
+    s.graph = g;
+    s.graph_threads = (int)t.threads;
+    s.graph_grid = (int)t.ctas;
+    return KGPU_OK;
+}
+
+int launch_slot(kgpu::BatchSlot& s, size_t n, cudaStream_t stream) {
+    const size_t bytes = batch_bytes((uint32_t)n);
+    bool ok = cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.n_copy, s.d_buf, s.h_buf, bytes,
+                                                 cudaMemcpyHostToDevice) == cudaSuccess;
+    cudaMemsetParams mp{};
+    mp.dst = s.d_status;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = n;
+    mp.height = 1;
+    ok = ok && cudaGraphExecMemsetNodeSetParams(s.exec, s.n_status_clear, &mp) == cudaSuccess;
+    ok = ok && cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.n_status_out, s.h_status, s.d_status, n * sizeof(int),
+                                                  cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok = ok && cudaGraphLaunch(s.exec, stream) == cudaSuccess;
+    ok = ok && cudaEventRecord(s.done, stream) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    return KGPU_OK;
+}
+
+}  // namespace
+
+namespace kgpu {
+namespace hostutil {
+
+void destroy_batch_slots(kgpu_ctx* ctx) {
+    for (auto& s : ctx->slots) free_slot(s);
+}
+
+}  // namespace hostutil
+}  // namespace kgpu
+
+extern "C" {
+
+int kgpu_set_tuning(kgpu_ctx* ctx, const kgpu_tuning* t) {
+    if (!ctx || !t) return KGPU_EINVAL;
+    int rc = tuning_ok(t);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    ctx->tune = *t;
+    return KGPU_OK;
+}
+
+int kgpu_get_tuning(kgpu_ctx* ctx, kgpu_tuning* t) {
+    if (!ctx || !t) return KGPU_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    *t = effective(ctx);
+    return KGPU_OK;
+}
+
+int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream stream, kgpu_ticket* out,
+                int* req_status) {
+    if (!ctx || !out || (n && !reqs) || n > (1u << 24)) return KGPU_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    DeviceGuard g(ctx->device);
+    const kgpu_tuning t = effective(ctx);
+    const uint64_t ticket = ++ctx->next_ticket;
+    kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
+    // rotate: the slot's previous batch must have finished before its
+    // staging buffers are refilled
+    if (s.issued && cudaEventSynchronize(s.done) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    s.issued = false;
+    int rc = prepare_slot(ctx, s, n ? n : 1, t);
+    if (rc) return rc;
+    rc = pack_batch(ctx, reqs, n, t.tile_chunks, s.h_buf, req_status);
+    if (rc) return rc;
+    s.nreq = (uint32_t)n;
+    s.gen = ticket;
+    if (n) {
+        if ((rc = launch_slot(s, n, (cudaStream_t)stream))) return rc;
+    } else if (cudaEventRecord(s.done, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    s.issued = true;
+    *out = ticket;
+    return KGPU_OK;
+}
+
+int kgpu_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* req_status) {
+    if (!ctx) return KGPU_EINVAL;
+    cudaEvent_t ev;
+    {
+        std::lock_guard<std::mutex> lk(ctx->batch_mu);
+        kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
+        if (ticket == 0 || s.gen != ticket || !s.issued) return KGPU_ENOENT;
+        ev = s.done;
+    }
+    DeviceGuard g(ctx->device);
+    cudaError_t e;
+    if (timeout_ns < 0) {
+        e = cudaEventSynchronize(ev);
+    } else {
+        auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns);
+        for (;;) {
+            e = cudaEventQuery(ev);
+            if (e != cudaErrorNotReady || std::chrono::steady_clock::now() >= deadline) break;
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
+    if (e == cudaErrorNotReady) return KGPU_ETIMEDOUT;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
+    if (s.gen != ticket) return KGPU_ENOENT;
+    if (req_status && s.nreq) std::memcpy(req_status, s.h_status, s.nreq * sizeof(int));
+    return KGPU_OK;
+}
+
+int kgpu_autotune(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream stream, uint32_t iters,
+                  kgpu_tuning* best, float* best_ms) {
+    if (!ctx || !reqs || !n || !best || n > (1u << 24)) return KGPU_EINVAL;
+    for (size_t i = 0; i < n; i++)
+        if (reqs[i].src == reqs[i].dst && reqs[i].len) return KGPU_EINVAL;
+    if (iters == 0) iters = 3;
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t thread_opts[] = {512, 256};
+    const uint32_t tile_opts[] = {8, 16, 32, 64, 128};
+    size_t bytes = batch_bytes((uint32_t)n);
+    std::vector<uint8_t> hbuf(bytes);
+    uint8_t* dbuf = nullptr;
+    unsigned long long* ctr = nullptr;
+    int* status = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = KGPU_OK;
+    if (cudaMalloc(&dbuf, bytes) != cudaSuccess || cudaMalloc(&ctr, 16) != cudaSuccess ||
+        cudaMalloc(&status, n * sizeof(int)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        rc = KGPU_ENOMEM;
+    }
+    kgpu_tuning chosen = effective(ctx);
+    float chosen_ms = -1.f;
+    for (uint32_t tc : tile_opts) {
+        if (rc) break;
+        rc = pack_batch(ctx, reqs, n, tc, hbuf.data(), nullptr);
+        if (rc) break;
+        if (cudaMemcpy(dbuf, hbuf.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = KGPU_EIO;
+            break;
+        }
+        for (uint32_t th : thread_opts) {
+            BatchArgs a{};
+            a.buf = dbuf;
+            a.keys = ctx->d_keys;
+            a.max_keys = ctx->cfg.max_keys;
+            a.next_tile = ctr;
+            a.status = status;
+            float total = 0.f;
+            bool ok = true;
+            for (uint32_t it = 0; it <= iters && ok; it++) {
+                ok = cudaMemsetAsync(ctr, 0, 16, st) == cudaSuccess;
+                ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
+                ok = ok && launch_batch(a, (int)th, ctx->num_sms, st) == cudaSuccess;
+                ok = ok && cudaEventRecord(e1, st) == cudaSuccess;
+                ok = ok && cudaEventSynchronize(e1) == cudaSuccess;
+                float ms = 0.f;
+                ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                if (it) total += ms;  // the first run is the warm-up
+            }
+            if (!ok) {
+                cudaGetLastError();
+                rc = KGPU_EIO;
+                break;
+            }
+            float mean = total / iters;
+            if (chosen_ms < 0 || mean < chosen_ms) {
+                chosen_ms = mean;
+                chosen.threads = th;
+                chosen.tile_chunks = tc;
+                chosen.ctas = (uint32_t)ctx->num_sms;
+            }
+        }
+    }
+    if (dbuf) cudaFree(dbuf);
+    if (ctr) cudaFree(ctr);
+    if (status) cudaFree(status);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    ctx->tune = chosen;
+    *best = chosen;
+    if (best_ms) *best_ms = chosen_ms;
+    return KGPU_OK;
+}
+
+}  // extern "C"

@@ -1,14 +1,11 @@
 // Internal declarations shared by the library's translation units: kernel
-// parameter blocks, launch helpers and the context layout.  Not part of the
-// public C ABI (that is include/kgpu.h).
+// parameter blocks, device descriptor formats and launch helpers.  Not part of
+// the public C ABI (that is include/kgpu.h).
 #pragma once
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cstddef>
 #include <cstdint>
-#include <mutex>
-#include <vector>
 
 #include "kgpu.h"
 
@@ -17,14 +14,16 @@ namespace kgpu {
 constexpr int kMaxRoundKeyWords = 60;  // AES-256: 4 * (14 + 1)
 
 // Shared-memory footprint of the table layouts (see aes_device.cuh).
-constexpr size_t kSmemEnc = 2 * 65536;  // regions A, B
-constexpr size_t kSmemDec = 3 * 65536;  // regions A, B, C
+constexpr size_t kRegionBytes = 65536;
+constexpr size_t kSmemEnc = 2 * kRegionBytes;  // regions A, B
+constexpr size_t kSmemDec = 3 * kRegionBytes;  // regions A, B, C
 
+// Threads per CTA of the bulk kernels (one CTA per SM).
 constexpr int kBulkThreads = 1024;
 
 // Where dynamic shared memory starts in a CTA's shared window (the reserved
 // system area comes first); the kernels fold it into their load offsets.
-constexpr int kSmemReservedBytes = 1024;  // threads per CTA of the bulk kernels (one CTA per SM)
+constexpr int kSmemReservedBytes = 1024;
 
 // Parameters of the bulk XTS / ECB kernels (passed by value, read from the
 // constant bank).
@@ -50,15 +49,26 @@ struct CbcParams {
     uint32_t rk[kMaxRoundKeyWords];
 };
 
-// One device-side key record (batched and serving kernels read keys from HBM).
+// Key schedules as the unified (batched / serving) kernels read them from the
+// device key table.  "u-frame" layout, 60 words each:
+//   words 0..3            round 0 (whitening)
+//   words 4r..4r+3        middle round r (1 <= r < Nr), each word rotated right
+//                         by 16 bits (the kernels fold the rotation of the
+//                         T2/T3 half of the round into the key)
+//   words 56..59          final round Nr (fixed slot whatever Nr is)
+// Decryption schedules are also stored in the state order (0, 3, 2, 1), which
+// turns the inverse cipher into the same round shape as the forward one.
 struct DevKey {
-    uint32_t enc[kMaxRoundKeyWords];
-    uint32_t dec[kMaxRoundKeyWords];
-    uint32_t twk[kMaxRoundKeyWords];  // XTS tweak key (encryption order)
-    uint32_t nr;                      // 10, 12 or 14
-    uint32_t flags;                   // bit 0: XTS key, bit 1: live
-    uint32_t pad[2];
+    uint32_t encu[kMaxRoundKeyWords];
+    uint32_t decu[kMaxRoundKeyWords];
+    uint32_t twku[kMaxRoundKeyWords];  // XTS tweak key (forward cipher)
+    uint32_t nr;                       // 10, 12 or 14
+    uint32_t flags;                    // kKeyLive | kKeyXts
+    uint32_t gen;                      // bumped on every setkey of the slot
+    uint32_t pad;
 };
+constexpr uint32_t kKeyLive = 1u;
+constexpr uint32_t kKeyXts = 2u;
 
 struct HostKey {
     bool live = false;
@@ -69,13 +79,72 @@ struct HostKey {
     uint32_t twk[kMaxRoundKeyWords];
 };
 
+// One request of a batch or of the serving ring, as the device sees it.
+struct ReqDesc {
+    const uint4* src;
+    uint4* dst;
+    const uint4* ivs;       // CBC: one IV per page
+    uint64_t nblocks;       // len / 16
+    uint64_t first_sector;  // XTS: number of the first data unit
+    uint32_t unit_blocks;   // XTS data unit / CBC page, in 16-byte blocks
+    uint32_t key;           // key-table slot
+    uint32_t mode;          // KGPU_MODE_*
+    uint32_t dir;           // KGPU_ENCRYPT / KGPU_DECRYPT (XTS, ECB)
+    uint32_t tile_units;    // work units (32-block chunks or pages) per tile
+    uint32_t pad;
+};
+static_assert(sizeof(ReqDesc) == 64, "descriptor layout");
+
+// Work units of a request: XTS/ECB count 32-block chunks, CBC counts pages.
+__host__ __device__ inline uint64_t request_units(const ReqDesc& d) {
+    if (d.mode == KGPU_MODE_CBC_DEC || d.mode == KGPU_MODE_CBC_ENC) return d.nblocks / d.unit_blocks;
+    return (d.nblocks + 31) / 32;
+}
+
+// Header of a batch as copied to the device: the descriptors follow, then the
+// exclusive prefix of tiles per request (nreq + 1 entries).
+struct BatchHeader {
+    uint64_t total_tiles;
+    uint32_t nreq;
+    uint32_t pad;
+};
+
+// Byte layout of a batch on the device: header, descriptors, tile prefix.
+__host__ __device__ inline size_t batch_desc_offset() { return sizeof(BatchHeader); }
+__host__ __device__ inline size_t batch_prefix_offset(uint32_t nreq) {
+    return sizeof(BatchHeader) + (size_t)nreq * sizeof(ReqDesc);
+}
+__host__ __device__ inline size_t batch_bytes(uint32_t nreq) {
+    return batch_prefix_offset(nreq) + ((size_t)nreq + 1) * sizeof(uint64_t);
+}
+
+// Arguments of the unified batch kernel (fixed per staging slot, so a captured
+// graph never needs new kernel parameters; the request count is in the header).
+struct BatchArgs {
+    const uint8_t* buf;  // BatchHeader | ReqDesc[nreq] | uint64_t tile_start[nreq + 1]
+    const DevKey* keys;
+    uint32_t max_keys;
+    uint32_t pad;
+    unsigned long long* next_tile;  // work counter (zero before launch)
+    int* status;                    // per request: 0, or a negative KGPU_E* set by the kernel
+};
+
 // Launch entry points implemented in the kernel translation units.  They
 // return a cudaError_t from the launch.
 cudaError_t launch_xts(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
 cudaError_t launch_ecb(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
 cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
+cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s);
+const void* batch_kernel_fn(int threads);  // for CUDA-graph kernel nodes
 cudaError_t upload_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* isb4);
-cudaError_t configure_kernels();  // opt-in to large dynamic shared memory
+cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* sb4,
+                                  const uint32_t* isb4);
+cudaError_t configure_kernels();        // bulk kernels: opt-in to large dynamic shared memory
+cudaError_t configure_batch_kernels();  // unified kernels: likewise
+
+// Unified-kernel shared memory: three table regions plus one tweak-key slot
+// (240 B, padded to 256) per warp.
+inline size_t unified_smem_bytes(int threads) { return 3 * kRegionBytes + (size_t)(threads / 32) * 256; }
 
 }  // namespace kgpu
