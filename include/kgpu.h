@@ -237,6 +237,85 @@ int kgpu_get_tuning(kgpu_ctx *ctx, kgpu_tuning *t);
 int kgpu_autotune(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream stream, uint32_t iters,
                   kgpu_tuning *best, float *best_ms);
 
+/* ------------------------------------------------------------------------
+ * Serving loop: the paper's Non-Stop Kernel (section 3.1) -- a kernel that
+ * is launched once and receives requests as messages in pinned memory while
+ * it runs -- rebuilt with continuous batching and bounded waits.  Requests are
+ * published one by one into a ring of descriptors in pinned host memory that
+ * the device reads directly; a persistent kernel (one CTA per SM) claims them
+ * in tiles as they arrive, so requests that arrive while others are running
+ * are admitted as slots and memory free up and run alongside them.  While it
+ * runs the kernel occupies every SM: other kernels of the process wait.
+ * ---------------------------------------------------------------------- */
+
+typedef struct kgpu_serve_config {
+    uint32_t ring_slots;       /* ring capacity, power of two (0: the context's ring_slots) */
+    uint32_t tile_chunks;      /* XTS/ECB tile in 512-byte chunks (0: 8, i.e. 4 KiB) */
+    uint64_t admit_bytes;      /* cap on bytes in flight (0: the context's admit_bytes) */
+    uint64_t idle_timeout_ns;  /* the kernel exits after this long with nothing to do
+                                  (0: the context's idle_timeout_ns); it is relaunched
+                                  by the next submit or poll */
+    uint64_t lifetime_ns;      /* the kernel exits at a tile boundary after this long and is
+                                  relaunched (0: 30 s), so no launch runs unbounded */
+    uint32_t reserved[4];
+} kgpu_serve_config;
+
+typedef struct kgpu_serve_stats {
+    uint64_t submitted;       /* requests accepted */
+    uint64_t completed;       /* requests seen complete by the host */
+    uint64_t busy_refusals;   /* submits refused with KGPU_EBUSY */
+    uint64_t launches;        /* kernel launches (first launch + relaunches) */
+    uint64_t inflight_bytes;  /* bytes of requests accepted and not yet seen complete */
+    uint32_t running;         /* 1 while a kernel instance is believed to run */
+    uint32_t last_exit;       /* why the last instance exited: 1 stop, 2 idle, 3 lifetime */
+} kgpu_serve_stats;
+
+/* Allocate the ring and launch the serving kernel on a library-owned stream.
+ * cfg may be NULL.  KGPU_EBUSY if serving already runs on this context. */
+int kgpu_serve_start(kgpu_ctx *ctx, const kgpu_serve_config *cfg);
+
+/*
+ * Publish one request (kgpu_request as for kgpu_submit; len must be > 0).
+ * Returns KGPU_EBUSY -- nothing published, retry later -- when its ring slot is
+ * still in use or when admitting it would put more than admit_bytes in flight
+ * (a request larger than the cap is admitted when nothing else is in flight).
+ * *ticket identifies the request for kgpu_serve_poll.
+ */
+int kgpu_serve_submit(kgpu_ctx *ctx, const kgpu_request *req, kgpu_ticket *ticket);
+
+/*
+ * Wait for a served request.  timeout_ns: 0 = check once, < 0 = wait until
+ * done, > 0 = wait at most that long.  KGPU_OK when complete (*status, if not
+ * NULL: 0 or the request's KGPU_E* code; stamps, if not NULL: the device's
+ * %globaltimer at its first tile and at its completion, 0 when the slot has
+ * been reused since), KGPU_ETIMEDOUT while pending, KGPU_ENOENT for a ticket
+ * that was never issued.  Relaunches the kernel if it exited with work pending.
+ */
+int kgpu_serve_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *status, uint64_t *stamps);
+
+/* Wait (at most drain_timeout_ns; < 0: no limit) for every published request
+ * to complete, stop the kernel and free the ring.  KGPU_ETIMEDOUT if requests
+ * were still pending at the limit (the kernel is stopped all the same). */
+int kgpu_serve_stop(kgpu_ctx *ctx, int64_t drain_timeout_ns);
+
+int kgpu_serve_get_stats(kgpu_ctx *ctx, kgpu_serve_stats *out);
+
+/*
+ * Trace replay for measurements (open-loop load generation): request i is
+ * issued at arrival_ns[i] after the call starts -- through the serving ring
+ * (kgpu_replay_serve; serving must be started) or as its own kernel launch on
+ * one of nstreams streams (kgpu_replay_launches, the per-request baseline) --
+ * and latency_ns[i] receives the time from its arrival to the host seeing it
+ * complete, so queueing behind a busy GPU counts.  *wall_ns receives the time
+ * from the start to the last completion.  All requests are validated before
+ * the first is issued.  KGPU_ETIMEDOUT if not all completed within timeout_ns
+ * (their latency is then UINT64_MAX).
+ */
+int kgpu_replay_serve(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
+                      int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
+int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
+                         uint32_t nstreams, int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
+
 #if defined(__GNUC__)
 #pragma GCC visibility pop
 #endif

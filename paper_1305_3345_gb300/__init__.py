@@ -71,6 +71,24 @@ def request_dtype():
     return REQUEST_DTYPE
 
 
+class KgpuServeConfig(ctypes.Structure):
+    """kgpu_serve_config (include/kgpu.h)."""
+    _fields_ = [("ring_slots", ctypes.c_uint32), ("tile_chunks", ctypes.c_uint32),
+                ("admit_bytes", ctypes.c_uint64), ("idle_timeout_ns", ctypes.c_uint64),
+                ("lifetime_ns", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class KgpuServeStats(ctypes.Structure):
+    """kgpu_serve_stats (include/kgpu.h)."""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("busy_refusals", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("inflight_bytes", ctypes.c_uint64), ("running", ctypes.c_uint32),
+                ("last_exit", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class KgpuConfig(ctypes.Structure):
     _fields_ = [("max_keys", ctypes.c_uint32), ("ring_slots", ctypes.c_uint32),
                 ("admit_bytes", ctypes.c_uint64), ("idle_timeout_ns", ctypes.c_uint64),
@@ -111,6 +129,13 @@ def lib() -> ctypes.CDLL:
                 "kgpu_get_tuning": ([vp, ctypes.POINTER(KgpuTuning)], i32),
                 "kgpu_autotune": ([vp, vp, sz, vp, u32, ctypes.POINTER(KgpuTuning), ctypes.POINTER(ctypes.c_float)],
                                   i32),
+                "kgpu_serve_start": ([vp, vp], i32),
+                "kgpu_serve_submit": ([vp, vp, ctypes.POINTER(u64)], i32),
+                "kgpu_serve_poll": ([vp, u64, ctypes.c_int64, vp, vp], i32),
+                "kgpu_serve_stop": ([vp, ctypes.c_int64], i32),
+                "kgpu_serve_get_stats": ([vp, ctypes.POINTER(KgpuServeStats)], i32),
+                "kgpu_replay_serve": ([vp, vp, vp, sz, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
+                "kgpu_replay_launches": ([vp, vp, vp, sz, u32, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -296,6 +321,73 @@ def kgpu_autotune(ctx, reqs, stream=None, iters: int = 3):
     return best.as_dict(), ms.value
 
 
+def kgpu_serve_start(ctx, ring_slots=0, tile_chunks=0, admit_bytes=0, idle_timeout_ns=0, lifetime_ns=0) -> None:
+    cfg = KgpuServeConfig(ring_slots, tile_chunks, admit_bytes, idle_timeout_ns, lifetime_ns)
+    _check(lib().kgpu_serve_start(ctx, ctypes.byref(cfg)), "kgpu_serve_start")
+
+
+def kgpu_serve_submit(ctx, req) -> int:
+    """Publish one request (a KgpuRequest or a record of request_dtype()).
+    Returns the ticket; raises KgpuError (code EBUSY when refused: retry)."""
+    import numpy as np
+    if isinstance(req, np.ndarray) or isinstance(req, np.void):
+        arr = np.ascontiguousarray(np.asarray(req, dtype=request_dtype()).reshape(1))
+        ptr = arr.ctypes.data
+        keep = arr
+    else:
+        keep = req
+        ptr = ctypes.addressof(req)
+    t = ctypes.c_uint64()
+    rc = lib().kgpu_serve_submit(ctx, ptr, ctypes.byref(t))
+    del keep
+    _check(rc, "kgpu_serve_submit")
+    return t.value
+
+
+def kgpu_serve_poll(ctx, ticket: int, timeout_ns: int = -1):
+    """(rc, status, (t_first_tile, t_done)) -- rc 0 when complete, -110 while pending."""
+    st = ctypes.c_int()
+    stamps = (ctypes.c_uint64 * 2)()
+    rc = lib().kgpu_serve_poll(ctx, ticket, timeout_ns, ctypes.byref(st), stamps)
+    if rc not in (0, -110):
+        _check(rc, "kgpu_serve_poll")
+    return rc, st.value, (stamps[0], stamps[1])
+
+
+def kgpu_serve_stop(ctx, drain_timeout_ns: int = -1) -> int:
+    rc = lib().kgpu_serve_stop(ctx, drain_timeout_ns)
+    if rc not in (0, -110):
+        _check(rc, "kgpu_serve_stop")
+    return rc
+
+
+def kgpu_serve_get_stats(ctx) -> dict:
+    s = KgpuServeStats()
+    _check(lib().kgpu_serve_get_stats(ctx, ctypes.byref(s)), "kgpu_serve_get_stats")
+    return s.as_dict()
+
+
+def _replay(fn, ctx, reqs, arrival_ns, extra, timeout_ns):
+    import numpy as np
+    ptr, n, keep = _req_array(reqs)
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    lat = np.zeros(n, dtype=np.uint64)
+    wall = ctypes.c_uint64()
+    rc = fn(ctx, ptr, arr.ctypes.data, n, *extra, timeout_ns, lat.ctypes.data, ctypes.byref(wall))
+    del keep
+    return rc, lat, wall.value
+
+
+def kgpu_replay_serve(ctx, reqs, arrival_ns, timeout_ns: int = 60_000_000_000):
+    """Open-loop replay through the serving ring: (rc, latency_ns array, wall_ns)."""
+    return _replay(lib().kgpu_replay_serve, ctx, reqs, arrival_ns, (), timeout_ns)
+
+
+def kgpu_replay_launches(ctx, reqs, arrival_ns, nstreams: int = 8, timeout_ns: int = 60_000_000_000):
+    """Open-loop replay with one kernel launch per request: (rc, latency_ns, wall_ns)."""
+    return _replay(lib().kgpu_replay_launches, ctx, reqs, arrival_ns, (nstreams,), timeout_ns)
+
+
 class Context:
     """Owns one kgpu_ctx on a device; methods mirror the C ABI without the ctx."""
 
@@ -355,3 +447,24 @@ class Context:
 
     def autotune(self, reqs, stream=None, iters=3):
         return kgpu_autotune(self.handle, reqs, stream, iters)
+
+    def serve_start(self, **kw):
+        kgpu_serve_start(self.handle, **kw)
+
+    def serve_submit(self, req) -> int:
+        return kgpu_serve_submit(self.handle, req)
+
+    def serve_poll(self, ticket, timeout_ns=-1):
+        return kgpu_serve_poll(self.handle, ticket, timeout_ns)
+
+    def serve_stop(self, drain_timeout_ns=-1):
+        return kgpu_serve_stop(self.handle, drain_timeout_ns)
+
+    def serve_stats(self) -> dict:
+        return kgpu_serve_get_stats(self.handle)
+
+    def replay_serve(self, reqs, arrival_ns, timeout_ns=60_000_000_000):
+        return kgpu_replay_serve(self.handle, reqs, arrival_ns, timeout_ns)
+
+    def replay_launches(self, reqs, arrival_ns, nstreams=8, timeout_ns=60_000_000_000):
+        return kgpu_replay_launches(self.handle, reqs, arrival_ns, nstreams, timeout_ns)

@@ -73,6 +73,7 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
     if (rc == KGPU_OK) rc = from_cuda(upload_unified_tables(t.te0, t.td0, t.sb4, t.isb4));
     if (rc == KGPU_OK) rc = from_cuda(cudaMalloc(&ctx->d_keys, sizeof(DevKey) * ctx->cfg.max_keys));
     if (rc == KGPU_OK) rc = from_cuda(cudaMemset(ctx->d_keys, 0, sizeof(DevKey) * ctx->cfg.max_keys));
+    if (rc == KGPU_OK) rc = from_cuda(cudaStreamCreateWithFlags(&ctx->key_stream, cudaStreamNonBlocking));
     if (rc != KGPU_OK) {
         cudaGetLastError();
         kgpu_destroy(ctx);
@@ -85,6 +86,7 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
 
 int kgpu_destroy(kgpu_ctx* ctx) {
     if (!ctx) return KGPU_OK;
+    destroy_serve(ctx);
     {
         DeviceGuard g(ctx->device);
         for (int i = 0; i < kgpu_ctx::kStages; i++) {
@@ -95,6 +97,7 @@ int kgpu_destroy(kgpu_ctx* ctx) {
             if (ctx->staging[i]) cudaFree(ctx->staging[i]);
         }
         destroy_batch_slots(ctx);
+        if (ctx->key_stream) cudaStreamDestroy(ctx->key_stream);
         if (ctx->d_keys) cudaFree(ctx->d_keys);
     }
     delete ctx;
@@ -139,7 +142,9 @@ int kgpu_aes_setkey(kgpu_ctx* ctx, const uint8_t* key, size_t key_len, int xts, 
     }
     if (slot >= ctx->cfg.max_keys) return KGPU_ENOMEM;
     DeviceGuard g(ctx->device);
-    if (cudaMemcpy(ctx->d_keys + slot, &dk, sizeof(dk), cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpyAsync(ctx->d_keys + slot, &dk, sizeof(dk), cudaMemcpyHostToDevice, ctx->key_stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->key_stream) != cudaSuccess) {
         cudaGetLastError();
         return KGPU_EIO;
     }
@@ -152,15 +157,27 @@ int kgpu_aes_setkey(kgpu_ctx* ctx, const uint8_t* key, size_t key_len, int xts, 
 
 int kgpu_aes_delkey(kgpu_ctx* ctx, kgpu_key key) {
     if (!ctx) return KGPU_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (key == 0 || key > ctx->keys.size() || !ctx->keys[key - 1].live) return KGPU_ENOENT;
+    }
+    // Work that reads the device key record must finish first: batches in
+    // flight and requests already published to the serving ring.  Launches of
+    // the per-call entry points carry their schedule in the launch itself.
+    int rc = batches_quiesce(ctx);
+    if (!rc) rc = serve_quiesce(ctx, 60000000000ll);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (key == 0 || key > ctx->keys.size() || !ctx->keys[key - 1].live) return KGPU_ENOENT;
+    if (!ctx->keys[key - 1].live) return KGPU_ENOENT;
     DeviceGuard g(ctx->device);
-    // Device-side uses of the key are ordered before this by the device-wide
-    // synchronisation; the record is then wiped.
-    cudaDeviceSynchronize();
     DevKey zero;
     std::memset(&zero, 0, sizeof(zero));
-    cudaMemcpy(ctx->d_keys + (key - 1), &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    if (cudaMemcpyAsync(ctx->d_keys + (key - 1), &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->key_stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->key_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
     std::memset(&ctx->keys[key - 1], 0, sizeof(HostKey));
     ctx->keys[key - 1].live = false;
     return KGPU_OK;

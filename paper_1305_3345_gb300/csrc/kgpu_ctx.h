@@ -38,6 +38,35 @@ struct BatchSlot {
 
 constexpr int kBatchSlots = 4;
 
+// Serving state (kgpu_serve_*): the mapped host ring, the device counters and
+// the host's bookkeeping of what is in flight.
+struct ServeState {
+    bool started = false;
+    bool running = false;  // a kernel instance was launched and has not been seen to exit
+    cudaStream_t stream = nullptr;
+    cudaEvent_t kdone = nullptr;
+    uint8_t* host_mem = nullptr;  // pinned, mapped: hdr | slots | done_seq | status | t_start | t_done
+    uint8_t* dev_mem = nullptr;   // ServeDev | claim | fin
+    ServeHostHdr* hdr = nullptr;
+    ServeSlot* slots = nullptr;
+    unsigned long long* done_seq = nullptr;
+    int* status = nullptr;
+    unsigned long long* t_start = nullptr;
+    unsigned long long* t_done = nullptr;
+    ServeArgs args{};
+    uint32_t nslots = 0;
+    uint32_t tile_chunks = 8;
+    uint64_t admit_bytes = 0;
+    uint64_t next_seq = 0;
+    uint64_t inflight_bytes = 0;
+    std::vector<uint8_t> slot_busy;
+    std::vector<uint64_t> slot_seq, slot_len;
+    std::vector<uint64_t> outstanding;  // seqs published and not yet seen complete
+    uint64_t submitted = 0, completed = 0, busy_refusals = 0, launches = 0;
+    uint64_t last_alive_check = 0;  // ns; publish re-checks the kernel at most every 20 us
+    unsigned last_exit = 0;
+};
+
 }  // namespace kgpu
 
 struct kgpu_ctx {
@@ -47,6 +76,7 @@ struct kgpu_ctx {
     std::mutex mu;
     std::vector<kgpu::HostKey> keys;
     kgpu::DevKey* d_keys = nullptr;
+    cudaStream_t key_stream = nullptr;  // private non-blocking stream for key-table writes
 
     // host-resident pipeline (kgpu_aes_xts_crypt_host): three device staging
     // buffers on three streams -- one chunk being copied in, one transformed,
@@ -62,6 +92,10 @@ struct kgpu_ctx {
     kgpu::BatchSlot slots[kgpu::kBatchSlots];
     uint64_t next_ticket = 0;
     kgpu_tuning tune{};
+
+    // serving loop (kgpu_serve_*)
+    std::mutex serve_mu;
+    kgpu::ServeState serve;
 };
 
 
@@ -70,11 +104,14 @@ namespace hostutil {
 
 constexpr int kVersion = (0 << 16) | 3;
 
+// Makes ctx's device current for the scope (and binds its primary context to
+// the calling thread, which the driver-API range check needs on threads that
+// have made no CUDA call yet); restores the previous device afterwards.
 class DeviceGuard {
   public:
     explicit DeviceGuard(int dev) {
         cudaGetDevice(&prev_);
-        if (prev_ != dev) cudaSetDevice(dev);
+        cudaSetDevice(dev);
     }
     ~DeviceGuard() {
         int cur = -1;
@@ -115,6 +152,7 @@ inline AddressRangeFn address_range_fn() {
 // ctx's device.  [base, base + size) is the whole allocation.
 inline int device_allocation(const kgpu_ctx* ctx, const void* p, uintptr_t* base, size_t* size) {
     if (!p) return KGPU_EFAULT;
+    DeviceGuard g(ctx->device);
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -193,7 +231,35 @@ inline void fill_bulk(BulkParams* p, const HostKey& k, int dir, const void* src,
 }
 
 
+// Validated allocation ranges, built afresh for every call so that a range is
+// never trusted after the caller could have freed it.
+struct RangeCache {
+    std::vector<std::pair<uintptr_t, uintptr_t>> r;
+    int check(const kgpu_ctx* ctx, const void* p, size_t len) {
+        uintptr_t a = (uintptr_t)p, e = a + len;
+        if (!p || e < a) return KGPU_EFAULT;
+        for (auto& x : r)
+            if (a >= x.first && e <= x.second) return KGPU_OK;
+        uintptr_t base = 0;
+        size_t size = 0;
+        int rc = device_allocation(ctx, p, &base, &size);
+        if (rc) return rc;
+        r.emplace_back(base, base + size);
+        return e <= base + size ? KGPU_OK : KGPU_EFAULT;
+    }
+};
+
+// Validate one request and write its device descriptor (tile size in 512-B
+// chunks for XTS/ECB; CBC tiles derive from it).  kgpu_batch_api.cu.
+int make_desc(kgpu_ctx* ctx, const kgpu_request& q, RangeCache& rc, uint32_t tile_chunks, ReqDesc* d);
+
 void destroy_batch_slots(kgpu_ctx* ctx);  // kgpu_batch_api.cu
+void destroy_serve(kgpu_ctx* ctx);        // kgpu_serve_api.cu
+// Wait until every request published to the serving ring so far has completed
+// (no-op when serving is off).  kgpu_serve_api.cu.
+int serve_quiesce(kgpu_ctx* ctx, int64_t timeout_ns);
+// Wait for every issued batch slot.  kgpu_batch_api.cu.
+int batches_quiesce(kgpu_ctx* ctx);
 
 }  // namespace hostutil
 }  // namespace kgpu

@@ -129,6 +129,57 @@ struct BatchArgs {
     int* status;                    // per request: 0, or a negative KGPU_E* set by the kernel
 };
 
+// ---------------------------------------------------------------------------
+// Serving ring.  Descriptors, the published count and the completion words
+// live in pinned host memory mapped into the device address space (the
+// paper's message passing through pinned memory, section 3.1); the claim and
+// finish counters live in device memory.
+// ---------------------------------------------------------------------------
+struct ServeSlot {
+    ReqDesc d;
+    unsigned long long ntiles;  // tiles of this request
+    unsigned long long seq;     // request number (slot = seq & mask)
+    unsigned long long pad[6];
+};
+static_assert(sizeof(ServeSlot) == 128, "slot layout");
+
+struct ServeHostHdr {
+    unsigned long long head;       // requests published (host writes, release)
+    unsigned int stop;             // host asks the kernel to exit
+    unsigned int pad0;
+    unsigned long long exit_code;  // kernel writes why it exited (kServeExit*)
+    unsigned long long heartbeat;  // dispatcher's last %globaltimer
+    unsigned long long pad[4];
+};
+constexpr unsigned kServeExitStop = 1, kServeExitIdle = 2, kServeExitLifetime = 3;
+
+struct ServeDev {
+    unsigned long long head;        // dispatcher's copy of the host head
+    unsigned long long cursor;      // lowest request that may have unclaimed tiles
+    unsigned long long done_count;  // requests completed
+    unsigned int stop;              // 0 run, else a kServeExit* reason
+    unsigned int pad;
+};
+
+struct ServeArgs {
+    const ServeSlot* slots;           // [S], mapped host
+    ServeHostHdr* hh;                 // mapped host
+    unsigned long long* done_seq;     // [S], mapped host: seq + 1 once complete
+    int* status;                      // [S], mapped host
+    unsigned long long* t_start;      // [S], mapped host: %globaltimer at the first tile
+    unsigned long long* t_done;       // [S], mapped host: %globaltimer at completion
+    ServeDev* dev;
+    unsigned long long* claim;        // [S], device: (seq << 24) | tiles claimed
+    unsigned long long* fin;          // [S], device: (seq << 24) | tiles finished
+    const DevKey* keys;
+    uint32_t max_keys;
+    uint32_t slot_mask;
+    unsigned long long idle_ns;       // exit after this long with nothing to do
+    unsigned long long lifetime_ns;   // exit at a tile boundary after this long
+};
+constexpr int kServeTagShift = 24;
+constexpr uint64_t kServeMaxTiles = (1ull << kServeTagShift) - 8192;
+
 // Launch entry points implemented in the kernel translation units.  They
 // return a cudaError_t from the launch.
 cudaError_t launch_xts(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
@@ -137,6 +188,7 @@ cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s);
 const void* batch_kernel_fn(int threads);  // for CUDA-graph kernel nodes
+cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s);
 cudaError_t upload_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* isb4);
 cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* sb4,
                                   const uint32_t* isb4);

@@ -1,0 +1,595 @@
+// Serving loop host side (kgpu_serve_*) and the trace-replay load generators
+// (kgpu_replay_*).  The host validates requests, writes descriptors into the
+// mapped ring and publishes them; the persistent kernel in kgpu_unified.cu
+// does all the work and publishes completions back into the ring.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#include "kgpu_ctx.h"
+
+using namespace kgpu;
+using namespace kgpu::hostutil;
+
+namespace {
+
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+template <class T>
+T load_acquire(const T* p) {
+    return __atomic_load_n(p, __ATOMIC_ACQUIRE);
+}
+
+template <class T>
+void store_release(T* p, T v) {
+    __atomic_store_n(p, v, __ATOMIC_RELEASE);
+}
+
+void cpu_relax() { std::this_thread::yield(); }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void serve_free(ServeState& st) {
+    if (st.stream) {
+        cudaStreamSynchronize(st.stream);
+        cudaStreamDestroy(st.stream);
+    }
+    if (st.kdone) cudaEventDestroy(st.kdone);
+    if (st.host_mem) cudaFreeHost(st.host_mem);
+    if (st.dev_mem) cudaFree(st.dev_mem);
+    st = ServeState();
+}
+
+int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
+    kgpu_serve_config c{};
+    if (cfg) c = *cfg;
+    uint32_t S = c.ring_slots ? c.ring_slots : ctx->cfg.ring_slots;
+    if (S < 2 || (S & (S - 1)) || S > (1u << 20)) return KGPU_EINVAL;
+    st.nslots = S;
+    st.tile_chunks = c.tile_chunks ? c.tile_chunks : 8;
+    if (st.tile_chunks > (1u << 20)) return KGPU_EINVAL;
+    st.admit_bytes = c.admit_bytes ? c.admit_bytes : ctx->cfg.admit_bytes;
+    const uint64_t idle = c.idle_timeout_ns ? c.idle_timeout_ns : ctx->cfg.idle_timeout_ns;
+    const uint64_t life = c.lifetime_ns ? c.lifetime_ns : 30000000000ull;
+
+    const size_t o_slots = 128;
+    const size_t o_done = o_slots + (size_t)S * sizeof(ServeSlot);
+    const size_t o_status = o_done + (size_t)S * 8;
+    const size_t o_tstart = align_up(o_status + (size_t)S * 4, 128);
+    const size_t o_tdone = o_tstart + (size_t)S * 8;
+    const size_t host_bytes = o_tdone + (size_t)S * 8;
+    const size_t d_claim = 128, d_fin = d_claim + (size_t)S * 8, dev_bytes = d_fin + (size_t)S * 8;
+
+    if (cudaHostAlloc(&st.host_mem, host_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
+        cudaMalloc(&st.dev_mem, dev_bytes) != cudaSuccess ||
+        cudaMemset(st.dev_mem, 0, dev_bytes) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&st.kdone, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        serve_free(st);
+        return KGPU_ENOMEM;
+    }
+    std::memset(st.host_mem, 0, host_bytes);
+    uint8_t* dmap = nullptr;
+    if (cudaHostGetDevicePointer((void**)&dmap, st.host_mem, 0) != cudaSuccess) {
+        cudaGetLastError();
+        serve_free(st);
+        return KGPU_EIO;
+    }
+    st.hdr = reinterpret_cast<ServeHostHdr*>(st.host_mem);
+    st.slots = reinterpret_cast<ServeSlot*>(st.host_mem + o_slots);
+    st.done_seq = reinterpret_cast<unsigned long long*>(st.host_mem + o_done);
+    st.status = reinterpret_cast<int*>(st.host_mem + o_status);
+    st.t_start = reinterpret_cast<unsigned long long*>(st.host_mem + o_tstart);
+    st.t_done = reinterpret_cast<unsigned long long*>(st.host_mem + o_tdone);
+
+    ServeArgs& a = st.args;
+    a = ServeArgs{};
+    a.slots = reinterpret_cast<const ServeSlot*>(dmap + o_slots);
+    a.hh = reinterpret_cast<ServeHostHdr*>(dmap);
+    a.done_seq = reinterpret_cast<unsigned long long*>(dmap + o_done);
+    a.status = reinterpret_cast<int*>(dmap + o_status);
+    a.t_start = reinterpret_cast<unsigned long long*>(dmap + o_tstart);
+    a.t_done = reinterpret_cast<unsigned long long*>(dmap + o_tdone);
+    a.dev = reinterpret_cast<ServeDev*>(st.dev_mem);
+    a.claim = reinterpret_cast<unsigned long long*>(st.dev_mem + d_claim);
+    a.fin = reinterpret_cast<unsigned long long*>(st.dev_mem + d_fin);
+    a.keys = ctx->d_keys;
+    a.max_keys = ctx->cfg.max_keys;
+    a.slot_mask = S - 1;
+    a.idle_ns = idle;
+    a.lifetime_ns = life;
+
+    st.slot_busy.assign(S, 0);
+    st.slot_seq.assign(S, 0);
+    st.slot_len.assign(S, 0);
+    st.outstanding.clear();
+    st.outstanding.reserve(S);
+    st.started = true;
+    return KGPU_OK;
+}
+
+// (Re)launch the serving kernel if no instance is running.  Caller holds serve_mu.
+int ensure_running(kgpu_ctx* ctx, ServeState& st) {
+    if (st.running) {
+        cudaError_t e = cudaEventQuery(st.kdone);
+        if (e == cudaErrorNotReady) return KGPU_OK;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return KGPU_EIO;
+        }
+        st.running = false;
+        st.last_exit = (unsigned)load_acquire(&st.hdr->exit_code);
+    }
+    store_release(&st.hdr->stop, 0u);
+    store_release(&st.hdr->exit_code, 0ull);
+    DeviceGuard g(ctx->device);
+    if (cudaMemsetAsync(&reinterpret_cast<ServeDev*>(st.dev_mem)->stop, 0, sizeof(unsigned int), st.stream) !=
+            cudaSuccess ||
+        launch_serve(st.args, 512, ctx->num_sms, st.stream) != cudaSuccess ||
+        cudaEventRecord(st.kdone, st.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    st.running = true;
+    st.launches++;
+    return KGPU_OK;
+}
+
+// Retire every outstanding request whose completion the device has published.
+void reap(ServeState& st) {
+    size_t w = 0;
+    for (size_t i = 0; i < st.outstanding.size(); i++) {
+        const uint64_t seq = st.outstanding[i];
+        const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
+        if (load_acquire(&st.done_seq[s]) >= seq + 1) {
+            st.slot_busy[s] = 0;
+            st.inflight_bytes -= st.slot_len[s];
+            st.completed++;
+        } else {
+            st.outstanding[w++] = seq;
+        }
+    }
+    st.outstanding.resize(w);
+}
+
+// Publish a validated descriptor.  Caller holds serve_mu.
+int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) {
+    const uint64_t len = d.nblocks * 16;
+    const uint64_t units = request_units(d);
+    const uint64_t nt = (units + d.tile_units - 1) / d.tile_units;
+    if (nt == 0 || nt > kServeMaxTiles) return KGPU_EINVAL;
+    const uint64_t seq = st.next_seq;
+    const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
+    auto refused = [&]() {
+        return st.slot_busy[s] || (st.inflight_bytes > 0 && st.inflight_bytes + len > st.admit_bytes);
+    };
+    if (refused()) {
+        reap(st);
+        if (refused()) {
+            st.busy_refusals++;
+            return KGPU_EBUSY;
+        }
+    }
+    ServeSlot& sl = st.slots[s];
+    sl.d = d;
+    sl.ntiles = nt;
+    sl.seq = seq;
+    st.status[s] = 0;
+    st.t_start[s] = 0;
+    st.t_done[s] = 0;
+    store_release(&st.hdr->head, (unsigned long long)(seq + 1));
+    st.slot_busy[s] = 1;
+    st.slot_seq[s] = seq;
+    st.slot_len[s] = len;
+    st.inflight_bytes += len;
+    st.outstanding.push_back(seq);
+    st.next_seq++;
+    st.submitted++;
+    *seq_out = seq;
+    const uint64_t t = now_ns();
+    if (!st.running || t - st.last_alive_check > 20000) {
+        st.last_alive_check = t;
+        return ensure_running(ctx, st);
+    }
+    return KGPU_OK;
+}
+
+}  // namespace
+
+namespace kgpu {
+namespace hostutil {
+
+int serve_quiesce(kgpu_ctx* ctx, int64_t timeout_ns) {
+    std::unique_lock<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    if (!st.started) return KGPU_OK;
+    const uint64_t upto = st.next_seq, t0 = now_ns();
+    for (;;) {
+        reap(st);
+        bool pending = false;
+        for (uint64_t seq : st.outstanding) pending |= seq < upto;
+        if (!pending) return KGPU_OK;
+        if (timeout_ns >= 0 && now_ns() - t0 >= (uint64_t)timeout_ns) return KGPU_ETIMEDOUT;
+        if (ensure_running(ctx, st)) return KGPU_EIO;
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        lk.lock();
+        if (!st.started) return KGPU_OK;
+    }
+}
+
+void destroy_serve(kgpu_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    if (!st.started) return;
+    store_release(&st.hdr->stop, 1u);
+    serve_free(st);
+}
+
+}  // namespace hostutil
+}  // namespace kgpu
+
+extern "C" {
+
+int kgpu_serve_start(kgpu_ctx* ctx, const kgpu_serve_config* cfg) {
+    if (!ctx) return KGPU_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    if (ctx->serve.started) return KGPU_EBUSY;
+    DeviceGuard g(ctx->device);
+    int rc = serve_alloc(ctx, ctx->serve, cfg);
+    if (rc) return rc;
+    rc = ensure_running(ctx, ctx->serve);
+    if (rc) serve_free(ctx->serve);
+    return rc;
+}
+
+int kgpu_serve_submit(kgpu_ctx* ctx, const kgpu_request* req, kgpu_ticket* ticket) {
+    if (!ctx || !req || !ticket) return KGPU_EINVAL;
+    if (req->len == 0) return KGPU_EINVAL;
+    ReqDesc d;
+    RangeCache rc;
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    if (!st.started) return KGPU_EINVAL;
+    int r = make_desc(ctx, *req, rc, st.tile_chunks, &d);
+    if (r) return r;
+    uint64_t seq = 0;
+    r = publish(ctx, st, d, &seq);
+    if (r == KGPU_OK || r == KGPU_EIO) *ticket = seq + 1;
+    return r;
+}
+
+int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* status, uint64_t* stamps) {
+    if (!ctx) return KGPU_EINVAL;
+    ServeState& st = ctx->serve;
+    {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        if (!st.started || ticket == 0 || ticket > st.next_seq) return KGPU_ENOENT;
+    }
+    const uint64_t seq = ticket - 1;
+    const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
+    const uint64_t t0 = now_ns();
+    uint64_t last_check = t0;
+    for (;;) {
+        const unsigned long long d = load_acquire(&st.done_seq[s]);
+        if (d >= seq + 1) {
+            const bool same = d == seq + 1;
+            if (status) *status = same ? load_acquire(&st.status[s]) : 0;
+            if (stamps) {
+                stamps[0] = same ? load_acquire(&st.t_start[s]) : 0;
+                stamps[1] = same ? load_acquire(&st.t_done[s]) : 0;
+            }
+            return KGPU_OK;
+        }
+        const uint64_t t = now_ns();
+        if (timeout_ns == 0 || t - last_check > 50000) {
+            std::lock_guard<std::mutex> lk(ctx->serve_mu);
+            if (!st.started) return KGPU_ENOENT;
+            reap(st);
+            if (!st.outstanding.empty()) {
+                int rc = ensure_running(ctx, st);
+                if (rc) return rc;
+            }
+            last_check = t;
+        }
+        if (timeout_ns == 0 || (timeout_ns > 0 && t - t0 >= (uint64_t)timeout_ns)) return KGPU_ETIMEDOUT;
+        cpu_relax();
+    }
+}
+
+int kgpu_serve_stop(kgpu_ctx* ctx, int64_t drain_timeout_ns) {
+    if (!ctx) return KGPU_EINVAL;
+    std::unique_lock<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    if (!st.started) return KGPU_OK;
+    const uint64_t t0 = now_ns();
+    int rc = KGPU_OK;
+    for (;;) {
+        reap(st);
+        if (st.outstanding.empty()) break;
+        if (drain_timeout_ns >= 0 && now_ns() - t0 >= (uint64_t)drain_timeout_ns) {
+            rc = KGPU_ETIMEDOUT;
+            break;
+        }
+        if (ensure_running(ctx, st)) {
+            rc = KGPU_EIO;
+            break;
+        }
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        lk.lock();
+    }
+    store_release(&st.hdr->stop, 1u);
+    DeviceGuard g(ctx->device);
+    if (cudaEventSynchronize(st.kdone) != cudaSuccess) {
+        cudaGetLastError();
+        if (!rc) rc = KGPU_EIO;
+    }
+    serve_free(st);
+    return rc;
+}
+
+int kgpu_serve_get_stats(kgpu_ctx* ctx, kgpu_serve_stats* out) {
+    if (!ctx || !out) return KGPU_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    std::memset(out, 0, sizeof(*out));
+    if (!st.started) return KGPU_OK;
+    reap(st);
+    if (st.running && cudaEventQuery(st.kdone) == cudaSuccess) {
+        st.running = false;
+        st.last_exit = (unsigned)load_acquire(&st.hdr->exit_code);
+    }
+    cudaGetLastError();
+    out->submitted = st.submitted;
+    out->completed = st.completed;
+    out->busy_refusals = st.busy_refusals;
+    out->launches = st.launches;
+    out->inflight_bytes = st.inflight_bytes;
+    out->running = st.running ? 1u : 0u;
+    out->last_exit = st.last_exit;
+    return KGPU_OK;
+}
+
+int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
+                      int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns) {
+    if (!ctx || !reqs || !arrival_ns || !latency_ns || !n) return KGPU_EINVAL;
+    std::vector<ReqDesc> descs(n);
+    uint32_t tile_chunks;
+    uint32_t nslots;
+    {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        if (!ctx->serve.started) return KGPU_EINVAL;
+        tile_chunks = ctx->serve.tile_chunks;
+        nslots = ctx->serve.nslots;
+    }
+    {
+        RangeCache rc;
+        for (size_t i = 0; i < n; i++) {
+            if (reqs[i].len == 0) return KGPU_EINVAL;
+            int r = make_desc(ctx, reqs[i], rc, tile_chunks, &descs[i]);
+            if (r) return r;
+            if (i && arrival_ns[i] < arrival_ns[i - 1]) return KGPU_EINVAL;
+        }
+    }
+    ServeState& st = ctx->serve;
+    std::unique_ptr<std::atomic<uint64_t>[]> seq_of(new std::atomic<uint64_t>[n]);
+    for (size_t i = 0; i < n; i++) {
+        seq_of[i].store(UINT64_MAX, std::memory_order_relaxed);
+        latency_ns[i] = UINT64_MAX;
+    }
+    std::atomic<size_t> produced{0};
+    std::atomic<bool> abort{false};
+    std::atomic<int> error{0};
+    const uint64_t t0 = now_ns();
+    const uint64_t deadline = timeout_ns > 0 ? t0 + (uint64_t)timeout_ns : UINT64_MAX;
+    uint64_t last_done = t0;
+
+    std::thread consumer([&]() {
+        std::vector<size_t> pending;
+        size_t seen = 0, done = 0;
+        uint64_t last_check = now_ns();
+        while (done < n) {
+            const size_t p = produced.load(std::memory_order_acquire);
+            while (seen < p) pending.push_back(seen++);
+            size_t w = 0;
+            const uint64_t t = now_ns();
+            for (size_t k = 0; k < pending.size(); k++) {
+                const size_t i = pending[k];
+                const uint64_t seq = seq_of[i].load(std::memory_order_acquire);
+                if (load_acquire(&st.done_seq[seq & (nslots - 1)]) >= seq + 1) {
+                    latency_ns[i] = t - (t0 + arrival_ns[i]);
+                    last_done = t;
+                    done++;
+                } else {
+                    pending[w++] = i;
+                }
+            }
+            pending.resize(w);
+            if (t - last_check > 100000) {  // relaunch the kernel if it exited with work pending
+                std::lock_guard<std::mutex> lk(ctx->serve_mu);
+                if (!pending.empty() && ensure_running(ctx, st)) error.store(KGPU_EIO);
+                last_check = t;
+            }
+            if (abort.load() || error.load() || t > deadline) break;
+        }
+    });
+
+    int rc = KGPU_OK;
+    for (size_t i = 0; i < n && !rc; i++) {
+        const uint64_t target = t0 + arrival_ns[i];
+        for (;;) {
+            const uint64_t t = now_ns();
+            if (t >= target) break;
+            if (target - t > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        for (;;) {
+            uint64_t seq = 0;
+            int r;
+            {
+                std::lock_guard<std::mutex> lk(ctx->serve_mu);
+                r = publish(ctx, st, descs[i], &seq);
+            }
+            if (r == KGPU_OK) {
+                seq_of[i].store(seq, std::memory_order_release);
+                produced.store(i + 1, std::memory_order_release);
+                break;
+            }
+            if (r != KGPU_EBUSY) {
+                rc = r;
+                break;
+            }
+            if (now_ns() > deadline) {
+                rc = KGPU_ETIMEDOUT;
+                break;
+            }
+            cpu_relax();
+        }
+        if (error.load()) rc = error.load();
+    }
+    if (rc) abort.store(true);
+    consumer.join();
+    if (!rc && error.load()) rc = error.load();
+    if (!rc) {
+        for (size_t i = 0; i < n; i++)
+            if (latency_ns[i] == UINT64_MAX) rc = KGPU_ETIMEDOUT;
+    }
+    if (wall_ns) *wall_ns = last_done - t0;
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    reap(st);
+    return rc;
+}
+
+int kgpu_replay_launches(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
+                         uint32_t nstreams, int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns) {
+    if (!ctx || !reqs || !arrival_ns || !latency_ns || !n || nstreams == 0 || nstreams > 256) return KGPU_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        if (ctx->serve.started) return KGPU_EBUSY;  // the serving kernel holds every SM
+    }
+    std::vector<ReqDesc> descs(n);
+    std::vector<HostKey> keys;
+    {
+        RangeCache rc;
+        for (size_t i = 0; i < n; i++) {
+            if (reqs[i].len == 0) return KGPU_EINVAL;
+            int r = make_desc(ctx, reqs[i], rc, 32, &descs[i]);
+            if (r) return r;
+            if (i && arrival_ns[i] < arrival_ns[i - 1]) return KGPU_EINVAL;
+        }
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        keys = ctx->keys;
+    }
+    DeviceGuard g(ctx->device);
+    std::vector<cudaStream_t> streams(nstreams, nullptr);
+    const size_t P = std::min<size_t>(n, 8192);
+    std::vector<cudaEvent_t> events(P, nullptr);
+    int rc = KGPU_OK;
+    for (auto& s : streams)
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) rc = KGPU_EIO;
+    for (auto& e : events)
+        if (!rc && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = KGPU_EIO;
+    for (size_t i = 0; i < n; i++) latency_ns[i] = UINT64_MAX;
+    std::unique_ptr<std::atomic<uint8_t>[]> fin(new std::atomic<uint8_t>[n]);
+    for (size_t i = 0; i < n; i++) fin[i].store(0);
+    std::atomic<size_t> issued{0};
+    std::atomic<bool> abort{false};
+    const uint64_t t0 = now_ns();
+    const uint64_t deadline = timeout_ns > 0 ? t0 + (uint64_t)timeout_ns : UINT64_MAX;
+    uint64_t last_done = t0;
+
+    std::thread consumer([&]() {
+        std::vector<size_t> next(nstreams);
+        for (uint32_t k = 0; k < nstreams; k++) next[k] = k;
+        size_t done = 0;
+        while (done < n && !abort.load()) {
+            const size_t iss = issued.load(std::memory_order_acquire);
+            for (uint32_t k = 0; k < nstreams; k++) {
+                while (next[k] < iss) {
+                    cudaError_t e = cudaEventQuery(events[next[k] % P]);
+                    if (e == cudaErrorNotReady) break;
+                    const uint64_t t = now_ns();
+                    latency_ns[next[k]] = t - (t0 + arrival_ns[next[k]]);
+                    last_done = t;
+                    fin[next[k]].store(1, std::memory_order_release);
+                    next[k] += nstreams;
+                    done++;
+                }
+            }
+            if (now_ns() > deadline) break;
+        }
+    });
+
+    for (size_t i = 0; i < n && !rc; i++) {
+        const uint64_t target = t0 + arrival_ns[i];
+        while (now_ns() < target) {
+            if (target - now_ns() > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        if (i >= P) {  // the event slot is free once request i - P is seen complete
+            while (!fin[i - P].load(std::memory_order_acquire)) {
+                if (now_ns() > deadline) {
+                    rc = KGPU_ETIMEDOUT;
+                    break;
+                }
+                cpu_relax();
+            }
+            if (rc) break;
+        }
+        const ReqDesc& d = descs[i];
+        const HostKey& k = keys[d.key];
+        cudaStream_t s = streams[i % nstreams];
+        cudaError_t e;
+        if (d.mode == KGPU_MODE_XTS || d.mode == KGPU_MODE_ECB) {
+            BulkParams p;
+            fill_bulk(&p, k, (int)d.dir, d.src, d.dst, d.nblocks * 16, (size_t)d.unit_blocks * 16, d.first_sector);
+            e = d.mode == KGPU_MODE_XTS ? launch_xts(p, k.nr, (int)d.dir, ctx->num_sms, s)
+                                        : launch_ecb(p, k.nr, (int)d.dir, ctx->num_sms, s);
+        } else {
+            CbcParams p;
+            std::memset(&p, 0, sizeof(p));
+            p.src = d.src;
+            p.dst = d.dst;
+            p.ivs = d.ivs;
+            p.npages = d.nblocks / d.unit_blocks;
+            p.bpp = d.unit_blocks;
+            const bool enc = d.mode == KGPU_MODE_CBC_ENC;
+            std::memcpy(p.rk, enc ? k.enc : k.dec, sizeof(p.rk));
+            e = enc ? launch_cbc_enc(p, k.nr, ctx->num_sms, s) : launch_cbc_dec(p, k.nr, ctx->num_sms, s);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(events[i % P], s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = KGPU_EIO;
+            break;
+        }
+        issued.store(i + 1, std::memory_order_release);
+    }
+    if (rc) abort.store(true);
+    consumer.join();
+    for (auto& s : streams)
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    for (auto& e : events)
+        if (e) cudaEventDestroy(e);
+    if (!rc) {
+        for (size_t i = 0; i < n; i++)
+            if (latency_ns[i] == UINT64_MAX) rc = KGPU_ETIMEDOUT;
+    }
+    if (wall_ns) *wall_ns = last_done - t0;
+    return rc;
+}
+
+}  // extern "C"

@@ -273,6 +273,209 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Serving kernel: the paper's Non-Stop Kernel (section 3.1) -- launched once,
+// fed through pinned host memory -- with every wait bounded.
+//
+// CTA 0 / warp 0 is the dispatcher: it polls the host-written request count
+// with system-scope acquire loads and mirrors it into device memory, so the
+// thousands of worker warps poll L2 instead of the host link.  Workers walk
+// the published requests in order; a request's tiles are claimed one at a time
+// with compare-and-swap on a per-slot word tagged with the request number (so
+// a warp that is late never touches the slot's next occupant), and the warp
+// that finishes the last tile publishes the completion to the host.  Requests
+// that arrive while others run are picked up as warps move past the ones that
+// are fully claimed: continuous batching at tile granularity.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ unsigned int ld_vol32(const unsigned int* p) {
+    return *reinterpret_cast<const volatile unsigned int*>(p);
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+constexpr long long kNoTile = -1, kRetry = -2;
+
+// Claim the next tile of request r (nt tiles) from its slot word.
+__device__ long long claim_tile(unsigned long long* w, unsigned long long r, unsigned long long nt) {
+    const unsigned long long mask = (1ull << kServeTagShift) - 1;
+    unsigned long long old = ld_vol(w);
+    for (int i = 0; i < 256; i++) {
+        const unsigned long long tag = old >> kServeTagShift;
+        if (tag > r) return kNoTile;  // r is retired and its slot reused
+        unsigned long long want, k;
+        if (tag < r) {                // slot still tagged with its previous occupant
+            k = 0;
+            want = (r << kServeTagShift) | 1ull;
+        } else {
+            k = old & mask;
+            if (k >= nt) return kNoTile;
+            want = old + 1;
+        }
+        const unsigned long long prev = atomicCAS(w, old, want);
+        if (prev == old) return (long long)k;
+        old = prev;
+        __nanosleep(32);
+    }
+    return kRetry;
+}
+
+// Count one finished tile of request r; returns the finished count.
+__device__ unsigned long long finish_tile(unsigned long long* w, unsigned long long r) {
+    const unsigned long long mask = (1ull << kServeTagShift) - 1;
+    unsigned long long old = ld_vol(w);
+    for (int i = 0; i < 4096; i++) {
+        if ((old >> kServeTagShift) == r) return (atomicAdd(w, 1ull) & mask) + 1;  // tag is stable now
+        const unsigned long long prev = atomicCAS(w, old, (r << kServeTagShift) | 1ull);
+        if (prev == old) return 1;
+        old = prev;
+    }
+    return 0;  // unreachable in practice: the finish word only moves forward to r
+}
+
+__device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
+    if (lane_id() != 0) return;
+    unsigned long long last = ld_vol(&a.dev->head);
+    unsigned long long idle_since = t0, backoff = 64;
+    unsigned int reason = 0;
+    for (;;) {
+        const unsigned long long now = gtimer();
+        const unsigned long long h = ld_acquire_sys(&a.hh->head);
+        if (h != last) {
+            st_release_gpu(&a.dev->head, h);
+            last = h;
+            idle_since = now;
+            backoff = 64;
+        }
+        if (ld_vol32(&a.hh->stop)) {
+            reason = kServeExitStop;
+            break;
+        }
+        const unsigned long long done = ld_vol(&a.dev->done_count);
+        if (done != last) idle_since = now;  // requests outstanding: not idle
+        if (now - idle_since > a.idle_ns && ld_acquire_sys(&a.hh->head) == last) {
+            reason = kServeExitIdle;
+            break;
+        }
+        if (now - t0 > a.lifetime_ns) {
+            reason = kServeExitLifetime;
+            break;
+        }
+        a.hh->heartbeat = now;
+        __nanosleep((unsigned)backoff);
+        if (backoff < 512) backoff <<= 1;
+    }
+    atomicExch(&a.dev->stop, reason);
+    a.hh->exit_code = reason;
+    __threadfence_system();
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant__ ServeArgs a) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;
+    fill_unified(smem);
+    __syncthreads();
+
+    const unsigned long long t0 = gtimer();
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && warp == 0) {
+        serve_dispatcher(a, t0);
+        return;
+    }
+    WarpKeys K;
+    K.twk = reinterpret_cast<const uint32_t*>(smem + 3 * kRegion + warp * 256);
+    K.nr = 0;
+    uint32_t cur_sel = 0xffffffffu;
+    unsigned long long r = ld_vol(&a.dev->cursor);
+    unsigned long long idle0 = 0;
+    unsigned int backoff = 32;
+    // workers give up on their own, later than the dispatcher's idle limit,
+    // should it ever stop answering
+    const unsigned long long own_idle = a.idle_ns + 1000000000ull;
+
+    for (;;) {
+        unsigned long long h = 0, now = 0;
+        unsigned int stop = 0;
+        if (lane == 0) {
+            h = ld_acquire_gpu(&a.dev->head);
+            stop = ld_vol32(&a.dev->stop);
+            now = gtimer();
+        }
+        h = __shfl_sync(0xffffffffu, h, 0);
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        now = __shfl_sync(0xffffffffu, now, 0);
+        if (stop || now - t0 > a.lifetime_ns) break;  // at a tile boundary: nothing held
+        if (r >= h) {
+            if (!idle0) idle0 = now;
+            else if (now - idle0 > own_idle) break;
+            __nanosleep(backoff);
+            if (backoff < 1024) backoff <<= 1;
+            unsigned long long c = lane == 0 ? ld_vol(&a.dev->cursor) : 0;
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if (c > r) r = c;
+            continue;
+        }
+        idle0 = 0;
+        backoff = 32;
+        const uint32_t s = (uint32_t)(r & a.slot_mask);
+        long long k = 0;
+        unsigned long long nt = 0;
+        if (lane == 0) {
+            const unsigned long long seq = ld_vol(&a.slots[s].seq);
+            nt = ld_vol(&a.slots[s].ntiles);
+            k = seq != r ? kNoTile : claim_tile(&a.claim[s], r, nt);
+        }
+        k = __shfl_sync(0xffffffffu, k, 0);
+        nt = __shfl_sync(0xffffffffu, nt, 0);
+        if (k == kRetry) {
+            __nanosleep(128);
+            continue;
+        }
+        if (k == kNoTile) {
+            if (lane == 0) atomicMax(&a.dev->cursor, r + 1);
+            r++;
+            continue;
+        }
+        const ReqDesc d = a.slots[s].d;
+        if (k == 0 && lane == 0) a.t_start[s] = gtimer();
+        const int st = run_tile(d, (uint64_t)k, a.keys, a.max_keys, K, cur_sel);
+        if (st && lane == 0) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
+        __syncwarp();
+        __threadfence();  // this tile's output is visible before it is counted
+        if (lane == 0 && finish_tile(&a.fin[s], r) == nt) {
+            a.t_done[s] = gtimer();
+            __threadfence_system();
+            st_release_sys(&a.done_seq[s], r + 1);
+            atomicAdd(&a.dev->done_count, 1ull);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* sb4,
@@ -288,6 +491,9 @@ cudaError_t configure_batch_kernels() {
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)unified_smem_bytes(512));
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(serve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)unified_smem_bytes(512));
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unified_smem_bytes(256));
     return e;
@@ -297,6 +503,12 @@ const void* batch_kernel_fn(int threads) {
     if (threads == 512) return reinterpret_cast<const void*>(batch_kernel<512>);
     if (threads == 256) return reinterpret_cast<const void*>(batch_kernel<256>);
     return nullptr;
+}
+
+cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s) {
+    if (threads != 512) return cudaErrorInvalidValue;
+    serve_kernel<512><<<grid, 512, unified_smem_bytes(512), s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s) {

@@ -1,0 +1,280 @@
+"""Serving loop: a persistent kernel fed through a ring in pinned host memory.
+
+Checks bit-exact results against the oracle, that every request's result is
+the same alone as in a concurrent mix, admission control (EBUSY), the bounded
+idle exit with transparent relaunch, and the trace-replay load generators.
+All buffers are prepared before serving starts: while the serving kernel runs
+it holds every SM, so the tests only copy memory meanwhile.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+class Traffic:
+    """Seeded requests (sizes log-uniform lo..hi, mixed modes and keys) over one
+    input pool, each with its own output region."""
+
+    def __init__(self, ctx, seed, n, lo, hi, nkeys, ecb=0.1):
+        import torch
+        import paper_1305_3345_gb300 as kg
+        self.ctx = ctx
+        mix = w.request_mix(seed, n, lo, hi, nkeys)
+        u = w.uniform01(seed, 98, n)
+        self.modes = np.where(u < ecb, w.MODE_ECB, mix.modes)
+        self.dirs, self.sizes, self.offsets, self.kidx = mix.dirs, mix.sizes, mix.offsets, mix.keys
+        self.keys, self.key_bits = w.mix_key_material(seed, mix), mix.key_bits
+        self.hx = [ctx.setkey(k[: 2 * b // 8], True) for k, b in zip(self.keys, self.key_bits)]
+        self.hs = [ctx.setkey(k[: b // 8], False) for k, b in zip(self.keys, self.key_bits)]
+        total = int(self.sizes.sum())
+        self.data = w.seeded_bytes(seed, w.STREAM_DATA, total)
+        self.src = torch.from_numpy(self.data.copy()).cuda()
+        self.out = [torch.zeros_like(self.src) for _ in range(2)]
+        npages = self.sizes // 4096
+        self.iv_off = np.concatenate([[0], np.cumsum(npages)[:-1]])
+        self.ivs_np = w.page_ivs(seed, int(npages.sum()))
+        self.ivs = torch.from_numpy(self.ivs_np.reshape(-1).copy()).cuda()
+        self.sectors = (w.u64(seed, 7, n) % (1 << 40)).astype(np.uint64)
+        torch.cuda.synchronize()
+        self.reqs = [self.request(i, 0) for i in range(n)]
+
+    def request(self, i, which):
+        import paper_1305_3345_gb300 as kg
+        r = np.zeros(1, dtype=kg.request_dtype())[0]
+        m, k = int(self.modes[i]), int(self.kidx[i])
+        r["mode"] = m
+        r["dir"] = int(self.dirs[i]) if m in (w.MODE_XTS, w.MODE_ECB) else 0
+        r["key"] = self.hx[k] if m == w.MODE_XTS else self.hs[k]
+        r["src"] = self.src.data_ptr() + int(self.offsets[i])
+        r["dst"] = self.out[which].data_ptr() + int(self.offsets[i])
+        r["len"] = int(self.sizes[i])
+        r["unit_size"] = 4096
+        r["sector"] = int(self.sectors[i])
+        r["ivs"] = self.ivs.data_ptr() + 16 * int(self.iv_off[i]) if m in (w.MODE_CBC_DEC, w.MODE_CBC_ENC) else 0
+        return r
+
+    def array(self, which=0):
+        import paper_1305_3345_gb300 as kg
+        a = np.zeros(len(self.reqs), dtype=kg.request_dtype())
+        for i in range(len(self.reqs)):
+            a[i] = self.request(i, which)
+        return a
+
+    def got(self, i, which=0):
+        a, b = int(self.offsets[i]), int(self.offsets[i] + self.sizes[i])
+        return self.out[which][a:b].cpu().numpy()
+
+    def expected(self, i):
+        m, k = int(self.modes[i]), int(self.kidx[i])
+        bits = int(self.key_bits[k])
+        a, b = int(self.offsets[i]), int(self.offsets[i] + self.sizes[i])
+        x = self.data[a:b]
+        if m == w.MODE_XTS:
+            return oracle.xts(self.keys[k][: 2 * bits // 8], int(self.dirs[i]), x, 4096, int(self.sectors[i]))
+        if m == w.MODE_ECB:
+            return oracle.ecb(self.keys[k][: bits // 8], int(self.dirs[i]), x)
+        p0 = int(self.iv_off[i])
+        return oracle.cbc(self.keys[k][: bits // 8], 0 if m == w.MODE_CBC_ENC else 1, x, 4096,
+                          self.ivs_np[p0:p0 + int(self.sizes[i]) // 4096])
+
+    def close(self):
+        for h in self.hx + self.hs:
+            self.ctx.delkey(h)
+
+
+def submit_retry(ctx, req, timeout_s=10.0):
+    import paper_1305_3345_gb300 as kg
+    t0 = time.time()
+    while True:
+        try:
+            return ctx.serve_submit(req)
+        except kg.KgpuError as e:
+            if e.code != "EBUSY" or time.time() - t0 > timeout_s:
+                raise
+            time.sleep(0.0001)
+
+
+def test_serve_one_by_one_vs_oracle(ctx):
+    t = Traffic(ctx, seed=71, n=40, lo=4096, hi=256 << 10, nkeys=8)
+    ctx.serve_start()
+    try:
+        for i, r in enumerate(t.reqs):
+            tk = ctx.serve_submit(r)
+            rc, st, stamps = ctx.serve_poll(tk, 10_000_000_000)
+            assert rc == 0 and st == 0
+            assert stamps[1] >= stamps[0] > 0
+            assert np.array_equal(t.got(i), t.expected(i)), (i, int(t.modes[i]))
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    t.close()
+
+
+def test_serve_same_alone_and_in_the_mix(ctx):
+    """Continuous batching: 200 requests submitted back to back run concurrently
+    on the device; each result equals the oracle and its result when it is the
+    only request in flight."""
+    t = Traffic(ctx, seed=73, n=200, lo=4096, hi=1 << 20, nkeys=32)
+    alone = t.array(which=1)
+    ctx.serve_start()
+    try:
+        tickets = [submit_retry(ctx, r) for r in t.reqs]
+        for tk in tickets:
+            rc, st, _ = ctx.serve_poll(tk, 20_000_000_000)
+            assert rc == 0 and st == 0
+        for i in range(len(t.reqs)):
+            tk = ctx.serve_submit(alone[i])
+            rc, st, _ = ctx.serve_poll(tk, 10_000_000_000)
+            assert rc == 0 and st == 0
+        stats = ctx.serve_stats()
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    assert stats["completed"] >= 2 * len(t.reqs) - 1
+    for i in range(len(t.reqs)):
+        mixed = t.got(i, 0)
+        assert np.array_equal(mixed, t.got(i, 1)), i
+        assert np.array_equal(mixed, t.expected(i)), (i, int(t.modes[i]))
+    t.close()
+
+
+def test_serve_admission_and_ring_limits(ctx):
+    import paper_1305_3345_gb300 as kg
+    t = Traffic(ctx, seed=79, n=64, lo=64 << 10, hi=256 << 10, nkeys=4)
+    ctx.serve_start(ring_slots=8, admit_bytes=256 << 10)
+    try:
+        tickets, refused = [], 0
+        for r in t.reqs:
+            while True:
+                try:
+                    tickets.append(ctx.serve_submit(r))
+                    break
+                except kg.KgpuError as e:
+                    assert e.code == "EBUSY"
+                    refused += 1
+                    ctx.serve_poll(tickets[-1], 1_000_000)   # let the oldest finish
+        for tk in tickets:
+            assert ctx.serve_poll(tk, 10_000_000_000)[0] == 0
+        stats = ctx.serve_stats()
+        assert stats["inflight_bytes"] == 0
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    assert refused > 0 and stats["busy_refusals"] == refused
+    for i in range(len(t.reqs)):
+        assert np.array_equal(t.got(i), t.expected(i)), i
+    t.close()
+
+
+def test_serve_idle_exit_and_relaunch(ctx):
+    t = Traffic(ctx, seed=83, n=6, lo=4096, hi=65536, nkeys=2)
+    ctx.serve_start(idle_timeout_ns=30_000_000, lifetime_ns=5_000_000_000)
+    try:
+        tk = ctx.serve_submit(t.reqs[0])
+        assert ctx.serve_poll(tk, 10_000_000_000)[0] == 0
+        time.sleep(0.4)                          # longer than the idle limit
+        stats = ctx.serve_stats()
+        assert stats["running"] == 0 and stats["last_exit"] == 2   # idle exit
+        for r in t.reqs[1:]:
+            tk = ctx.serve_submit(r)              # relaunches the kernel
+            assert ctx.serve_poll(tk, 10_000_000_000)[0] == 0
+        assert ctx.serve_stats()["launches"] >= 2
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    for i in range(len(t.reqs)):
+        assert np.array_equal(t.got(i), t.expected(i))
+    t.close()
+
+
+def test_serve_lifetime_bound_relaunches_transparently(ctx):
+    t = Traffic(ctx, seed=89, n=120, lo=4096, hi=128 << 10, nkeys=4)
+    ctx.serve_start(idle_timeout_ns=2_000_000_000, lifetime_ns=20_000_000)
+    try:
+        for r in t.reqs:
+            tk = ctx.serve_submit(r)
+            assert ctx.serve_poll(tk, 10_000_000_000)[0] == 0
+            time.sleep(0.001)
+        assert ctx.serve_stats()["launches"] >= 2
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    for i in range(len(t.reqs)):
+        assert np.array_equal(t.got(i), t.expected(i)), i
+    t.close()
+
+
+def test_serve_concurrent_submitters(ctx):
+    t = Traffic(ctx, seed=97, n=120, lo=4096, hi=128 << 10, nkeys=8)
+    ctx.serve_start()
+    errors = []
+
+    def worker(idx):
+        try:
+            for i in idx:
+                tk = submit_retry(ctx, t.reqs[i])
+                rc, st, _ = ctx.serve_poll(tk, 10_000_000_000)
+                assert rc == 0 and st == 0
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    ths = [threading.Thread(target=worker, args=(range(k, len(t.reqs), 4),)) for k in range(4)]
+    try:
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    assert not errors, errors
+    for i in range(len(t.reqs)):
+        assert np.array_equal(t.got(i), t.expected(i)), i
+    t.close()
+
+
+def test_replay_serve_and_launches(ctx):
+    """Open-loop Poisson replay (the serving workload's shape, scaled down):
+    both dispatch forms complete every request with identical bytes."""
+    n = 3000
+    t = Traffic(ctx, seed=5, n=n, lo=4096, hi=1 << 20, nkeys=64)
+    arr = (w.poisson_arrivals(5, n, 100_000.0) * 1e9).astype(np.uint64)
+    reqs0 = t.array(0)
+    reqs1 = t.array(1)
+    ctx.serve_start()
+    try:
+        rc, lat, wall = ctx.replay_serve(reqs0, arr)
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    assert rc == 0 and np.all(lat < np.uint64(10**10)) and wall > 0
+    rc, lat2, wall2 = ctx.replay_launches(reqs1, arr, nstreams=8)
+    assert rc == 0 and np.all(lat2 < np.uint64(10**10))
+    import torch
+    torch.cuda.synchronize()
+    assert torch.equal(t.out[0], t.out[1])
+    for i in list(range(0, n, 97)) + [n - 1]:
+        assert np.array_equal(t.got(i), t.expected(i)), i
+    t.close()
+
+
+def test_serve_rejects_bad_requests(ctx):
+    import paper_1305_3345_gb300 as kg
+    t = Traffic(ctx, seed=101, n=2, lo=4096, hi=8192, nkeys=1)
+    ctx.serve_start()
+    try:
+        r = t.reqs[0].copy()
+        r["len"] = 0
+        with pytest.raises(kg.KgpuError):
+            ctx.serve_submit(r)
+        r = t.reqs[0].copy()
+        r["key"] = 4000
+        with pytest.raises(kg.KgpuError):
+            ctx.serve_submit(r)
+        with pytest.raises(kg.KgpuError):
+            ctx.serve_start()            # already running
+        with pytest.raises(kg.KgpuError):
+            ctx.serve_poll(10**9, 0)      # never issued
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    t.close()
