@@ -50,6 +50,7 @@ typedef struct CUstream_st *kgpu_stream; /* a cudaStream_t */
 enum {
     KGPU_OK = 0,
     KGPU_EIO = -5,         /* CUDA launch or runtime failure */
+    KGPU_E2BIG = -7,       /* more requests than a fixed-size area holds */
     KGPU_ENOMEM = -12,     /* allocation failed or a table is full */
     KGPU_EFAULT = -14,     /* a pointer is not (wholly) inside a usable allocation */
     KGPU_EBUSY = -16,      /* queue full / admission refused: retry later */
@@ -315,6 +316,40 @@ int kgpu_replay_serve(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *a
                       int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
 int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
                          uint32_t nstreams, int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free batched submission.  No counterpart in the paper.
+ * ---------------------------------------------------------------------- */
+
+#define KGPU_NOALLOC_MAX_REQUESTS 512
+#define KGPU_NOALLOC_SCRATCH_BYTES 40960
+
+/*
+ * kgpu_submit for callers that cannot allocate memory when they call: for
+ * example an OS-level caller on a page-writeback or memory-reclaim path, which
+ * may need pages encrypted precisely because memory is short and whose
+ * allocation could block on the very reclaim it serves, or a deployment whose
+ * memory budget is fixed at start-up.  It runs the same persistent batch
+ * kernel, but its scratch (work counter, per-request status words, device copy
+ * of the descriptors) is one fixed array of KGPU_NOALLOC_SCRATCH_BYTES of
+ * device memory inside the library image, which every GPU that loads the
+ * library holds until the process exits; the descriptors are packed in a fixed
+ * host array.  The call makes no cudaMalloc/cudaFree or other allocating call.
+ *
+ * Arguments as kgpu_submit, without a ticket: the work is queued on `stream`
+ * and the caller synchronises on that stream.  At most
+ * KGPU_NOALLOC_MAX_REQUESTS requests per call: more is KGPU_E2BIG, with
+ * nothing launched.  Validation as kgpu_submit (req_status, if not NULL,
+ * receives each request's validation code); a key deleted while the batch runs
+ * is not reported back.  The counter and status words are cleared on every
+ * call, but every call shares the one array: calls whose work overlaps on the
+ * GPU (on different streams, or from different threads without ordering)
+ * race and corrupt each other -- order them on one stream or synchronise in
+ * between.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.
+ */
+int kgpu_submit_noalloc(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream stream, int *req_status);
 
 #if defined(__GNUC__)
 #pragma GCC visibility pop

@@ -24,7 +24,7 @@ MODE_CBC_ENC = 2
 MODE_ECB = 3
 
 _ERRORS = {
-    -5: "EIO", -12: "ENOMEM", -14: "EFAULT", -16: "EBUSY", -19: "ENODEV", -22: "EINVAL", -2: "ENOENT",
+    -5: "EIO", -7: "E2BIG", -12: "ENOMEM", -14: "EFAULT", -16: "EBUSY", -19: "ENODEV", -22: "EINVAL", -2: "ENOENT",
     -110: "ETIMEDOUT",
 }
 
@@ -136,6 +136,7 @@ def lib() -> ctypes.CDLL:
                 "kgpu_serve_get_stats": ([vp, ctypes.POINTER(KgpuServeStats)], i32),
                 "kgpu_replay_serve": ([vp, vp, vp, sz, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
                 "kgpu_replay_launches": ([vp, vp, vp, sz, u32, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
+                "kgpu_submit_noalloc": ([vp, vp, sz, vp, vp], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -321,6 +322,18 @@ def kgpu_autotune(ctx, reqs, stream=None, iters: int = 3):
     return best.as_dict(), ms.value
 
 
+NOALLOC_MAX_REQUESTS = 512
+
+
+def kgpu_submit_noalloc(ctx, reqs, stream=None, status=None) -> None:
+    """Allocation-free batched submission (queued on `stream`; synchronise on it)."""
+    ptr, n, keep = _req_array(reqs)
+    sp = status.ctypes.data if status is not None else None
+    rc = lib().kgpu_submit_noalloc(ctx, ptr, n, _stream(stream), sp)
+    del keep
+    _check(rc, "kgpu_submit_noalloc")
+
+
 def kgpu_serve_start(ctx, ring_slots=0, tile_chunks=0, admit_bytes=0, idle_timeout_ns=0, lifetime_ns=0) -> None:
     cfg = KgpuServeConfig(ring_slots, tile_chunks, admit_bytes, idle_timeout_ns, lifetime_ns)
     _check(lib().kgpu_serve_start(ctx, ctypes.byref(cfg)), "kgpu_serve_start")
@@ -447,6 +460,9 @@ class Context:
 
     def autotune(self, reqs, stream=None, iters=3):
         return kgpu_autotune(self.handle, reqs, stream, iters)
+
+    def submit_noalloc(self, reqs, stream=None, status=None):
+        kgpu_submit_noalloc(self.handle, reqs, stream, status)
 
     def serve_start(self, **kw):
         kgpu_serve_start(self.handle, **kw)

@@ -24,6 +24,7 @@ const char* kgpu_strerror(int code) {
     switch (code) {
         case KGPU_OK: return "success";
         case KGPU_EIO: return "CUDA launch or runtime failure";
+        case KGPU_E2BIG: return "too many requests for the fixed scratch area";
         case KGPU_ENOMEM: return "out of memory or table full";
         case KGPU_EFAULT: return "pointer not inside a usable allocation";
         case KGPU_EBUSY: return "busy: queue full or admission refused";

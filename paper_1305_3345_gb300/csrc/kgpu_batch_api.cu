@@ -196,58 +196,6 @@ int launch_slot(kgpu::BatchSlot& s, size_t n, cudaStream_t stream) {
 namespace kgpu {
 namespace hostutil {
 
-// Validate one request and write its device descriptor.
-int make_desc(kgpu_ctx* ctx, const kgpu_request& q, RangeCache& rc, uint32_t tile_chunks, ReqDesc* d) {
-    std::memset(d, 0, sizeof(*d));
-    if (q.flags) return KGPU_EINVAL;
-    const bool cbc = q.mode == KGPU_MODE_CBC_DEC || q.mode == KGPU_MODE_CBC_ENC;
-    const bool xts = q.mode == KGPU_MODE_XTS;
-    if (!xts && !cbc && q.mode != KGPU_MODE_ECB) return KGPU_EINVAL;
-    if ((xts || q.mode == KGPU_MODE_ECB) && q.dir != KGPU_ENCRYPT && q.dir != KGPU_DECRYPT) return KGPU_EINVAL;
-    uint64_t unit = q.mode == KGPU_MODE_ECB ? 16 : q.unit_size;
-    if (unit == 0 || unit % 16 || q.len % unit || unit / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
-    if (xts) {
-        uint64_t units = q.len / unit;
-        if (units && q.sector + (units - 1) < q.sector) return KGPU_EINVAL;
-    }
-    {
-        std::lock_guard<std::mutex> g(ctx->mu);
-        if (q.key == 0 || q.key > ctx->keys.size()) return KGPU_ENOENT;
-        const HostKey& k = ctx->keys[q.key - 1];
-        if (!k.live || k.xts != xts) return KGPU_ENOENT;
-    }
-    if (q.len) {
-        int r = check_pair(q.src, q.dst, q.len);
-        if (r) return r;
-        if ((r = rc.check(ctx, q.src, q.len)) || (r = rc.check(ctx, q.dst, q.len))) return r;
-        if (cbc) {
-            uint64_t npages = q.len / unit;
-            if ((uintptr_t)q.ivs & 15) return KGPU_EINVAL;
-            if ((r = rc.check(ctx, q.ivs, npages * 16))) return r;
-            uintptr_t iv0 = (uintptr_t)q.ivs, iv1 = iv0 + npages * 16, d0 = (uintptr_t)q.dst;
-            if (iv0 < d0 + q.len && d0 < iv1) return KGPU_EINVAL;
-        }
-    }
-    d->src = static_cast<const uint4*>(q.src);
-    d->dst = static_cast<uint4*>(q.dst);
-    d->ivs = reinterpret_cast<const uint4*>(q.ivs);
-    d->nblocks = q.len / 16;
-    d->first_sector = q.sector;
-    d->unit_blocks = (uint32_t)(unit / 16);
-    d->key = q.key - 1;
-    d->mode = q.mode;
-    d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : q.dir;
-    if (q.mode == KGPU_MODE_CBC_ENC) {
-        d->tile_units = 32;  // one chain per lane
-    } else if (q.mode == KGPU_MODE_CBC_DEC) {
-        uint64_t ppt = (uint64_t)tile_chunks * 32 / d->unit_blocks;
-        d->tile_units = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ppt, 1u << 30));
-    } else {
-        d->tile_units = std::max<uint32_t>(1, tile_chunks);
-    }
-    return KGPU_OK;
-}
-
 int batches_quiesce(kgpu_ctx* ctx) {
     std::lock_guard<std::mutex> lk(ctx->batch_mu);
     DeviceGuard g(ctx->device);

@@ -110,11 +110,11 @@ struct BatchHeader {
 };
 
 // Byte layout of a batch on the device: header, descriptors, tile prefix.
-__host__ __device__ inline size_t batch_desc_offset() { return sizeof(BatchHeader); }
-__host__ __device__ inline size_t batch_prefix_offset(uint32_t nreq) {
+__host__ __device__ constexpr size_t batch_desc_offset() { return sizeof(BatchHeader); }
+__host__ __device__ constexpr size_t batch_prefix_offset(uint32_t nreq) {
     return sizeof(BatchHeader) + (size_t)nreq * sizeof(ReqDesc);
 }
-__host__ __device__ inline size_t batch_bytes(uint32_t nreq) {
+__host__ __device__ constexpr size_t batch_bytes(uint32_t nreq) {
     return batch_prefix_offset(nreq) + ((size_t)nreq + 1) * sizeof(uint64_t);
 }
 
