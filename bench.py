@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary mode measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-requests comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sweep")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of each serving trace")
     ap.add_argument("--bytes", type=int, default=GIB,
                     help="buffer size (default 1 GiB; smaller only for profiler captures)")
     return ap.parse_args()
@@ -208,6 +211,153 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batched and serving workloads
+
+def pct(lat_ns):
+    a = np.sort(np.asarray(lat_ns, dtype=np.float64)) / 1e3
+    q = lambda p: float(a[min(len(a) - 1, int(np.ceil(p / 100 * len(a))) - 1)])
+    return {"p50_us": q(50), "p99_us": q(99), "p99.9_us": q(99.9), "max_us": float(a[-1])}
+
+
+def register_mix_keys(ctx, seed, mix):
+    keys = w.mix_key_material(seed, mix)
+    hx = np.array([ctx.setkey(k[: 2 * b // 8], True) for k, b in zip(keys, mix.key_bits)], dtype=np.uint32)
+    hs = np.array([ctx.setkey(k[: b // 8], False) for k, b in zip(keys, mix.key_bits)], dtype=np.uint32)
+    return hx, hs
+
+
+def build_requests(kg, mix, hx, hs, src, src_span, dst, dst_span, ivs, seed):
+    """Request records for a mix: inputs are page-aligned windows of `src`,
+    outputs go to `dst` at the cumulative offset (modulo dst_span), CBC IVs
+    are per page from `ivs` (cyclic)."""
+    n = len(mix.sizes)
+    r = np.zeros(n, dtype=kg.request_dtype())
+    win = (src_span - int(mix.sizes.max())) // 4096
+    src_off = (w.u64(seed, 8, n) % max(1, win)).astype(np.int64) * 4096
+    dst_off = (mix.offsets % (dst_span - int(mix.sizes.max()))) // 4096 * 4096
+    npages = mix.sizes // 4096
+    iv_pages = ivs.numel() // 16
+    iv_off = (np.concatenate([[0], np.cumsum(npages)[:-1]]) % max(1, iv_pages - int(npages.max())))
+    xts = mix.modes == w.MODE_XTS
+    r["mode"] = mix.modes
+    r["dir"] = np.where(xts, mix.dirs, 0)
+    r["key"] = np.where(xts, hx[mix.keys], hs[mix.keys])
+    r["src"] = src.data_ptr() + src_off
+    r["dst"] = dst.data_ptr() + dst_off
+    r["len"] = mix.sizes
+    r["unit_size"] = 4096
+    r["sector"] = mix.offsets // 4096
+    r["ivs"] = np.where(xts, 0, ivs.data_ptr() + 16 * iv_off)
+    return r
+
+
+def run_batched(ctx, kg, dev):
+    """10,000 requests, log-uniform 4 KiB..8 MiB, 256 keys (AES-128/256), modes
+    50% XTS / 25% CBC-dec / 25% CBC-enc: one persistent-kernel submission
+    (autotuned launch shape, CUDA-graph replay) vs one launch per request."""
+    import torch
+    n = 10000
+    mix = w.request_mix(4, n, 4096, 8 << 20, 256)
+    hx, hs = register_mix_keys(ctx, 4, mix)
+    src = torch.from_numpy(w.seeded_bytes(4, w.STREAM_DATA, GIB)).to(f"cuda:{dev}")
+    total = mix.total_bytes
+    dst = torch.empty(total + (8 << 20), dtype=torch.uint8, device=f"cuda:{dev}")
+    ivs = torch.from_numpy(w.page_ivs(4, int((mix.sizes // 4096).sum())).reshape(-1).copy()).to(f"cuda:{dev}")
+    reqs = build_requests(kg, mix, hx, hs, src, GIB, dst, dst.numel(), ivs, 4)
+    torch.cuda.synchronize()
+    best, tune_ms = ctx.autotune(reqs, iters=2)
+    # batched: submit -> poll, wall clock around the call pair (host packing,
+    # graph launch and the whole kernel), after one warm-up
+    t = ctx.submit(reqs)
+    ctx.poll(t, -1)
+    walls = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        t = ctx.submit(reqs)
+        ctx.poll(t, -1)
+        walls.append(time.perf_counter() - t0)
+    wall = min(walls)
+    # per-request launches: all 10,000 issued at once on 8 streams
+    arr = np.zeros(n, dtype=np.uint64)
+    ctx.replay_launches(reqs, arr, nstreams=8)           # warm-up
+    rc, lat, wall_pr = ctx.replay_launches(reqs, arr, nstreams=8)
+    out = {
+        "workload": "10000 requests, 4 KiB..8 MiB log-uniform (page multiples), 256 keys, "
+                    "50% XTS / 25% CBC-dec / 25% CBC-enc, seed 4",
+        "bytes": total,
+        "batched": {"GB/s": total / wall / 1e9, "ms": wall * 1e3, "latency_all_requests_ms": wall * 1e3,
+                    "tuning": best, "autotune_best_kernel_ms": tune_ms,
+                    "form": "one persistent-kernel launch via CUDA graph (kgpu_submit)"},
+        "per_request": {"GB/s": total / (wall_pr / 1e9) / 1e9, "ms": wall_pr / 1e6, "rc": rc,
+                        "latency": pct(lat), "form": "one kernel launch per request, 8 streams"},
+    }
+    for h in list(hx) + list(hs):
+        ctx.delkey(int(h))
+    del src, dst, ivs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(ctx, kg, dev, seconds):
+    """Poisson arrivals at 10k..1M requests/s, sizes log-uniform 4 KiB..1 MiB,
+    1,024 keys, admission cap 8 GiB in flight: the serving ring vs one launch
+    per request on the same trace (open loop, latency from arrival)."""
+    import torch
+    nkeys = 1024
+    pool_in, pool_out = GIB, 9 * GIB
+    src = torch.from_numpy(w.seeded_bytes(5, w.STREAM_DATA, pool_in)).to(f"cuda:{dev}")
+    dst = torch.empty(pool_out, dtype=torch.uint8, device=f"cuda:{dev}")
+    ivs = torch.from_numpy(w.page_ivs(5, 1 << 20).reshape(-1).copy()).to(f"cuda:{dev}")
+    key_mix = w.request_mix(5, 16, 4096, 1 << 20, nkeys)
+    hx, hs = register_mix_keys(ctx, 5, key_mix)
+    torch.cuda.synchronize()
+    res = []
+    for rate in (10_000, 100_000, 300_000, 1_000_000):
+        n = int(rate * seconds)
+        mix = w.request_mix(5 + rate, n, 4096, 1 << 20, nkeys)
+        mix.key_bits = key_mix.key_bits
+        reqs = build_requests(kg, mix, hx, hs, src, pool_in, dst, pool_out, ivs, 5 + rate)
+        arr = (w.poisson_arrivals(5 + rate, n, float(rate)) * 1e9).astype(np.uint64)
+        detail = np.zeros(3 * n, dtype=np.uint64)
+        ctx.serve_start(admit_bytes=8 * GIB)
+        try:
+            with ClockSampler(dev) as clk_ring:
+                rc, lat, wall = ctx.replay_serve(reqs, arr, timeout_ns=120_000_000_000, detail=detail)
+            stats = ctx.serve_stats()
+        finally:
+            ctx.serve_stop(30_000_000_000)
+        d = detail.reshape(n, 3).astype(np.int64)
+        service = d[:, 2] - d[:, 1]
+        by_mode = {}
+        for m, name in ((w.MODE_XTS, "xts"), (w.MODE_CBC_DEC, "cbc_dec"), (w.MODE_CBC_ENC, "cbc_enc")):
+            sel = mix.modes == m
+            if sel.any():
+                by_mode[name] = {"latency": pct(lat[sel]), "device_service": pct(service[sel])}
+        with ClockSampler(dev) as clk_pr:
+            rc2, lat2, wall2 = ctx.replay_launches(reqs, arr, nstreams=8, timeout_ns=120_000_000_000)
+        total = int(mix.sizes.sum())
+        res.append({
+            "rate_req_s": rate, "requests": n, "offered_GB/s": total / (float(arr[-1]) / 1e9) / 1e9,
+            "ring": {"GB/s": total / (wall / 1e9) / 1e9, "rc": rc, "latency": pct(lat),
+                     "host_wait_before_publish": pct(d[:, 0]), "device_service": pct(service),
+                     "by_mode": by_mode, "clocks": clk_ring.summary(),
+                     "busy_refusals": stats["busy_refusals"], "launches": stats["launches"]},
+            "per_request": {"GB/s": total / (wall2 / 1e9) / 1e9, "rc": rc2, "latency": pct(lat2),
+                            "clocks": clk_pr.summary(),
+                            "by_mode": {k: {"latency": pct(lat2[mix.modes == m])} for m, k in
+                                        ((w.MODE_XTS, "xts"), (w.MODE_CBC_DEC, "cbc_dec"),
+                                         (w.MODE_CBC_ENC, "cbc_enc")) if (mix.modes == m).any()}},
+        })
+    for h in list(hx) + list(hs):
+        ctx.delkey(int(h))
+    del src, dst, ivs
+    torch.cuda.empty_cache()
+    return {"workload": "Poisson arrivals, sizes 4 KiB..1 MiB log-uniform, 1024 keys (AES-128/256), "
+                        "50% XTS / 25% CBC-dec / 25% CBC-enc, admission cap 8 GiB, "
+                        f"{seconds:g} s per rate",
+            "rates": res}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def time_op(fn, iters: int, stream):
@@ -363,6 +513,12 @@ def run_kgpu(args):
                        "d2h_bytes_per_step": GIB, "steps": e2e_steps, "chunk_bytes": chunk,
                        "call": "kgpu_aes_xts_crypt_host (pinned host pages)"}
         del hsrc, hdst
+
+    if rank == 0 and not args.no_batched and nbytes == GIB:
+        line["batched"] = run_batched(ctx, kg, dev)
+
+    if rank == 0 and not args.no_serve and nbytes == GIB:
+        line["serving"] = run_serving(ctx, kg, dev, args.serve_seconds)
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate()

@@ -185,7 +185,7 @@ typedef struct kgpu_request {
 
 /* Launch shape of the persistent batch kernel (see kgpu_autotune). */
 typedef struct kgpu_tuning {
-    uint32_t threads;      /* threads per CTA: 256 or 512 (default 512) */
+    uint32_t threads;      /* threads per CTA: 512 or 1024 (default 1024) */
     uint32_t tile_chunks;  /* work per XTS/ECB tile in 512-byte chunks (default 32 = 16 KiB);
                               CBC-decrypt tiles hold the same bytes in whole pages,
                               CBC-encrypt tiles hold up to 32 pages (one chain per lane) */
@@ -310,10 +310,13 @@ int kgpu_serve_get_stats(kgpu_ctx *ctx, kgpu_serve_stats *out);
  * complete, so queueing behind a busy GPU counts.  *wall_ns receives the time
  * from the start to the last completion.  All requests are validated before
  * the first is issued.  KGPU_ETIMEDOUT if not all completed within timeout_ns
- * (their latency is then UINT64_MAX).
+ * (their latency is then UINT64_MAX).  kgpu_replay_serve can also fill
+ * detail[3 * i ...] (if not NULL) with: the time request i waited on the host
+ * before it was published (ns, admission and ring limits included), and the
+ * device's %globaltimer when its first tile started and when it completed.
  */
 int kgpu_replay_serve(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
-                      int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
+                      int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns, uint64_t *detail);
 int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
                          uint32_t nstreams, int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
 

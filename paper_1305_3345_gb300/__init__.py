@@ -134,7 +134,7 @@ def lib() -> ctypes.CDLL:
                 "kgpu_serve_poll": ([vp, u64, ctypes.c_int64, vp, vp], i32),
                 "kgpu_serve_stop": ([vp, ctypes.c_int64], i32),
                 "kgpu_serve_get_stats": ([vp, ctypes.POINTER(KgpuServeStats)], i32),
-                "kgpu_replay_serve": ([vp, vp, vp, sz, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
+                "kgpu_replay_serve": ([vp, vp, vp, sz, ctypes.c_int64, vp, ctypes.POINTER(u64), vp], i32),
                 "kgpu_replay_launches": ([vp, vp, vp, sz, u32, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
                 "kgpu_submit_noalloc": ([vp, vp, sz, vp, vp], i32),
             }
@@ -380,20 +380,26 @@ def kgpu_serve_get_stats(ctx) -> dict:
     return s.as_dict()
 
 
-def _replay(fn, ctx, reqs, arrival_ns, extra, timeout_ns):
+def _replay(fn, ctx, reqs, arrival_ns, extra, timeout_ns, detail=None):
     import numpy as np
     ptr, n, keep = _req_array(reqs)
     arr = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
     lat = np.zeros(n, dtype=np.uint64)
     wall = ctypes.c_uint64()
-    rc = fn(ctx, ptr, arr.ctypes.data, n, *extra, timeout_ns, lat.ctypes.data, ctypes.byref(wall))
+    tail = (detail.ctypes.data,) if detail is not None else ()
+    rc = fn(ctx, ptr, arr.ctypes.data, n, *extra, timeout_ns, lat.ctypes.data, ctypes.byref(wall), *tail)
     del keep
     return rc, lat, wall.value
 
 
-def kgpu_replay_serve(ctx, reqs, arrival_ns, timeout_ns: int = 60_000_000_000):
-    """Open-loop replay through the serving ring: (rc, latency_ns array, wall_ns)."""
-    return _replay(lib().kgpu_replay_serve, ctx, reqs, arrival_ns, (), timeout_ns)
+def kgpu_replay_serve(ctx, reqs, arrival_ns, timeout_ns: int = 60_000_000_000, detail=None):
+    """Open-loop replay through the serving ring: (rc, latency_ns array, wall_ns).
+    detail: optional uint64 array of 3*n (host wait before publish, device
+    first-tile stamp, device completion stamp)."""
+    import numpy as np
+    if detail is None:
+        detail = np.zeros(3 * (len(reqs)), dtype=np.uint64)
+    return _replay(lib().kgpu_replay_serve, ctx, reqs, arrival_ns, (), timeout_ns, detail)
 
 
 def kgpu_replay_launches(ctx, reqs, arrival_ns, nstreams: int = 8, timeout_ns: int = 60_000_000_000):
@@ -479,8 +485,8 @@ class Context:
     def serve_stats(self) -> dict:
         return kgpu_serve_get_stats(self.handle)
 
-    def replay_serve(self, reqs, arrival_ns, timeout_ns=60_000_000_000):
-        return kgpu_replay_serve(self.handle, reqs, arrival_ns, timeout_ns)
+    def replay_serve(self, reqs, arrival_ns, timeout_ns=60_000_000_000, detail=None):
+        return kgpu_replay_serve(self.handle, reqs, arrival_ns, timeout_ns, detail)
 
     def replay_launches(self, reqs, arrival_ns, nstreams=8, timeout_ns=60_000_000_000):
         return kgpu_replay_launches(self.handle, reqs, arrival_ns, nstreams, timeout_ns)

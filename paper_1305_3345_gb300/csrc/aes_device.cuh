@@ -259,55 +259,45 @@ __device__ __forceinline__ uint32_t uni_col(uint32_t a, uint32_t b, uint32_t c, 
     return lds_tab<kSmemBase>(row_addr<0>(a, L.r0)) ^ lds_tab<kSmemBase>(row_addr<1>(b, L.r1)) ^ rotl16(hi);
 }
 
-// Round keys in registers (compile-time indices after unrolling).
-struct RegKey {
-    uint32_t w_[kMaxKeyWords];
-    __device__ __forceinline__ uint32_t w(int i) const { return w_[i]; }
-    __device__ __forceinline__ void load(const uint32_t* g) {
-        const uint4* g4 = reinterpret_cast<const uint4*>(g);
-#pragma unroll
-        for (int i = 0; i < kMaxKeyWords / 4; i++) {
-            uint4 v = g4[i];
-            w_[4 * i] = v.x;
-            w_[4 * i + 1] = v.y;
-            w_[4 * i + 2] = v.z;
-            w_[4 * i + 3] = v.w;
-        }
-    }
-};
-
-// Round keys in this warp's shared-memory slot (generic pointer into shared).
-struct SmemKey {
-    const uint32_t* p;
-    __device__ __forceinline__ uint32_t w(int i) const { return p[i]; }
-};
+// Round key r (16 bytes, four words) from a 16-byte-aligned key slot in
+// shared memory: one broadcast LDS.128.
+__device__ __forceinline__ uint4 round_key(uint32_t slot_saddr, int r) {
+    uint4 k;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(k.x), "=r"(k.y), "=r"(k.z), "=r"(k.w)
+                 : "r"(slot_saddr + 16u * (uint32_t)r));
+    return k;
+}
 
 // One block through the cipher of the unified layout (u-frame state and key).
-template <class Key>
-__device__ __forceinline__ void cipher_u(uint32_t& u0, uint32_t& u1, uint32_t& u2, uint32_t& u3, const Key& k,
-                                         int nr, const UniLanes& L) {
-    u0 ^= k.w(0);
-    u1 ^= k.w(1);
-    u2 ^= k.w(2);
-    u3 ^= k.w(3);
-#pragma unroll
-    for (int r = 1; r < 14; r++) {
-        if (r < nr) {
-            uint32_t t0 = uni_col(u0, u1, u2, u3, k.w(4 * r + 0), L);
-            uint32_t t1 = uni_col(u1, u2, u3, u0, k.w(4 * r + 1), L);
-            uint32_t t2 = uni_col(u2, u3, u0, u1, k.w(4 * r + 2), L);
-            uint32_t t3 = uni_col(u3, u0, u1, u2, k.w(4 * r + 3), L);
-            u0 = t0;
-            u1 = t1;
-            u2 = t2;
-            u3 = t3;
-        }
+// The round count is a run-time value and the rounds are a real loop with the
+// round key read from shared memory: the body is one round, which keeps the
+// kernels that serve every mode small enough to stay in the instruction cache.
+__device__ __forceinline__ void cipher_u(uint32_t& u0, uint32_t& u1, uint32_t& u2, uint32_t& u3,
+                                         uint32_t key_saddr, int nr, const UniLanes& L) {
+    uint4 k = round_key(key_saddr, 0);
+    u0 ^= k.x;
+    u1 ^= k.y;
+    u2 ^= k.z;
+    u3 ^= k.w;
+#pragma unroll 1
+    for (int r = 1; r < nr; r++) {
+        k = round_key(key_saddr, r);
+        const uint32_t t0 = uni_col(u0, u1, u2, u3, k.x, L);
+        const uint32_t t1 = uni_col(u1, u2, u3, u0, k.y, L);
+        const uint32_t t2 = uni_col(u2, u3, u0, u1, k.z, L);
+        const uint32_t t3 = uni_col(u3, u0, u1, u2, k.w, L);
+        u0 = t0;
+        u1 = t1;
+        u2 = t2;
+        u3 = t3;
     }
+    k = round_key(key_saddr, 14);  // the final round key sits in words 56..59
 #define KGPU_FIN(P, x) lds_tab<kSmemBase>(row_addr<P>(x, L.f))
-    uint32_t o0 = merge_bytes(KGPU_FIN(0, u0), KGPU_FIN(1, u1), KGPU_FIN(2, u2), KGPU_FIN(3, u3)) ^ k.w(56);
-    uint32_t o1 = merge_bytes(KGPU_FIN(0, u1), KGPU_FIN(1, u2), KGPU_FIN(2, u3), KGPU_FIN(3, u0)) ^ k.w(57);
-    uint32_t o2 = merge_bytes(KGPU_FIN(0, u2), KGPU_FIN(1, u3), KGPU_FIN(2, u0), KGPU_FIN(3, u1)) ^ k.w(58);
-    uint32_t o3 = merge_bytes(KGPU_FIN(0, u3), KGPU_FIN(1, u0), KGPU_FIN(2, u1), KGPU_FIN(3, u2)) ^ k.w(59);
+    const uint32_t o0 = merge_bytes(KGPU_FIN(0, u0), KGPU_FIN(1, u1), KGPU_FIN(2, u2), KGPU_FIN(3, u3)) ^ k.x;
+    const uint32_t o1 = merge_bytes(KGPU_FIN(0, u1), KGPU_FIN(1, u2), KGPU_FIN(2, u3), KGPU_FIN(3, u0)) ^ k.y;
+    const uint32_t o2 = merge_bytes(KGPU_FIN(0, u2), KGPU_FIN(1, u3), KGPU_FIN(2, u0), KGPU_FIN(3, u1)) ^ k.z;
+    const uint32_t o3 = merge_bytes(KGPU_FIN(0, u3), KGPU_FIN(1, u0), KGPU_FIN(2, u1), KGPU_FIN(3, u2)) ^ k.w;
 #undef KGPU_FIN
     u0 = o0;
     u1 = o1;
@@ -316,14 +306,13 @@ __device__ __forceinline__ void cipher_u(uint32_t& u0, uint32_t& u1, uint32_t& u
 }
 
 // Block in natural column order through the unified cipher in direction dir.
-template <class Key>
-__device__ __forceinline__ void cipher_block(uint4& v, const Key& k, int nr, const UniLanes& L, int dir) {
+__device__ __forceinline__ void cipher_block(uint4& v, uint32_t key_saddr, int nr, const UniLanes& L, int dir) {
     if (dir) {
         uint32_t t = v.y;
         v.y = v.w;
         v.w = t;
     }
-    cipher_u(v.x, v.y, v.z, v.w, k, nr, L);
+    cipher_u(v.x, v.y, v.z, v.w, key_saddr, nr, L);
     if (dir) {
         uint32_t t = v.y;
         v.y = v.w;

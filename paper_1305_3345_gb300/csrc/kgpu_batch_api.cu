@@ -18,7 +18,7 @@ namespace {
 
 kgpu_tuning default_tuning(const kgpu_ctx* ctx) {
     kgpu_tuning t{};
-    t.threads = 512;
+    t.threads = 1024;
     t.tile_chunks = 32;
     t.ctas = (uint32_t)ctx->num_sms;
     return t;
@@ -34,7 +34,7 @@ kgpu_tuning effective(const kgpu_ctx* ctx) {
 }
 
 int tuning_ok(const kgpu_tuning* t) {
-    if (t->threads && t->threads != 256 && t->threads != 512) return KGPU_EINVAL;
+    if (t->threads && t->threads != 512 && t->threads != 1024) return KGPU_EINVAL;
     if (t->tile_chunks > (1u << 20)) return KGPU_EINVAL;
     if (t->ctas > 4096) return KGPU_EINVAL;
     return KGPU_OK;
@@ -307,7 +307,7 @@ int kgpu_autotune(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream
     std::lock_guard<std::mutex> lk(ctx->batch_mu);
     DeviceGuard g(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const uint32_t thread_opts[] = {512, 256};
+    const uint32_t thread_opts[] = {1024, 512};
     const uint32_t tile_opts[] = {8, 16, 32, 64, 128};
     size_t bytes = batch_bytes((uint32_t)n);
     std::vector<uint8_t> hbuf(bytes);

@@ -243,18 +243,28 @@ __global__ void __launch_bounds__(kBulkThreads, 1) cbc_enc_kernel(const __grid_c
     const uint64_t ngroups = (p.npages + 31) >> 5;
 
     for (uint64_t g = interleaved_warp(); g < ngroups; g += total_warps()) {
+        // lanes without a page step along with the others, loads and stores
+        // predicated off, so the warp stays converged through the chain
         const uint64_t page = (g << 5) + lane;
-        if (page >= p.npages) continue;  // no shuffles below: divergence is fine
-        const uint4* in = p.src + page * bpp;
-        uint4* out = p.dst + page * bpp;
-        uint4 x = p.ivs[page];
-        uint4 nxt = in[0];
+        const bool valid = page < p.npages;
+        const uint4* in = p.src + (valid ? page : 0) * bpp;
+        uint4* out = p.dst + (valid ? page : 0) * bpp;
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        uint4 x = valid ? p.ivs[page] : z;
+        // the chain is sequential, so plaintext is fetched four blocks ahead
+        uint4 q0 = valid ? in[0] : z;
+        uint4 q1 = valid && bpp > 1 ? in[1] : z;
+        uint4 q2 = valid && bpp > 2 ? in[2] : z;
+        uint4 q3 = valid && bpp > 3 ? in[3] : z;
         for (uint32_t i = 0; i < bpp; ++i) {
-            const uint4 cur = nxt;
-            if (i + 1 < bpp) nxt = in[i + 1];
+            const uint4 cur = q0;
+            q0 = q1;
+            q1 = q2;
+            q2 = q3;
+            if (valid && i + 4 < bpp) q3 = in[i + 4];
             xor4(x, cur.x, cur.y, cur.z, cur.w);
             encrypt_block<NR>(x.x, x.y, x.z, x.w, T, K);
-            out[i] = x;
+            if (valid) out[i] = x;
         }
     }
 }

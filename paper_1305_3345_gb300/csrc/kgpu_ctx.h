@@ -56,6 +56,7 @@ struct ServeState {
     unsigned long long* t_done = nullptr;
     ServeArgs args{};
     uint32_t nslots = 0;
+    uint64_t tile_ring = 0;  // entries of the device tile ring
     uint32_t tile_chunks = 8;
     uint64_t admit_bytes = 0;
     uint64_t next_seq = 0;

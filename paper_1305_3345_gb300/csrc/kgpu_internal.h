@@ -139,7 +139,8 @@ struct ServeSlot {
     ReqDesc d;
     unsigned long long ntiles;  // tiles of this request
     unsigned long long seq;     // request number (slot = seq & mask)
-    unsigned long long pad[6];
+    unsigned long long pos0;    // device copy only: tile-ring position of its first tile
+    unsigned long long pad[5];
 };
 static_assert(sizeof(ServeSlot) == 128, "slot layout");
 
@@ -153,32 +154,44 @@ struct ServeHostHdr {
 };
 constexpr unsigned kServeExitStop = 1, kServeExitIdle = 2, kServeExitLifetime = 3;
 
+// Each counter sits on its own 128-byte line: idle workers poll tile_head
+// while busy ones update the others, and one shared line would serialise them.
 struct ServeDev {
-    unsigned long long head;        // dispatcher's copy of the host head
-    unsigned long long cursor;      // lowest request that may have unclaimed tiles
-    unsigned long long done_count;  // requests completed
-    unsigned int stop;              // 0 run, else a kServeExit* reason
-    unsigned int pad;
+    alignas(128) unsigned long long tile_head;   // tiles published to the tile ring (dispatcher, release)
+    alignas(128) unsigned long long tile_next;   // tiles claimed by workers (atomicAdd)
+    alignas(128) unsigned long long tile_done;   // tiles finished
+    alignas(128) unsigned long long mirrored;    // requests copied to device memory and enumerated
+    alignas(128) unsigned long long done_count;  // requests completed
+    alignas(128) unsigned int stop;              // 0 run, else a kServeExit* reason
 };
 
 struct ServeArgs {
-    const ServeSlot* slots;           // [S], mapped host
+    const ServeSlot* slots;           // [S], mapped host: descriptors as the host wrote them
     ServeHostHdr* hh;                 // mapped host
     unsigned long long* done_seq;     // [S], mapped host: seq + 1 once complete
     int* status;                      // [S], mapped host
-    unsigned long long* t_start;      // [S], mapped host: %globaltimer at the first tile
+    unsigned long long* t_start;      // [S], mapped host: %globaltimer when its first tile starts
     unsigned long long* t_done;       // [S], mapped host: %globaltimer at completion
     ServeDev* dev;
-    unsigned long long* claim;        // [S], device: (seq << 24) | tiles claimed
-    unsigned long long* fin;          // [S], device: (seq << 24) | tiles finished
+    ServeSlot* dslots;                // [S], device copy of the descriptors
+    unsigned long long* fin;          // [S], device: tiles finished per request
+    unsigned long long* tiles;        // [T], device tile ring: (slot << 32) | tile
+    unsigned long long* mbox;         // [grid * 16], one 128-B line per CTA: published
+                                      // tile count, bit 63 = stop (polled by that CTA only)
     const DevKey* keys;
     uint32_t max_keys;
-    uint32_t slot_mask;
+    uint32_t slot_mask;               // S - 1
+    unsigned long long tile_mask;     // T - 1
+    uint32_t tile_bits;               // log2(T)
+    uint32_t pad1;
     unsigned long long idle_ns;       // exit after this long with nothing to do
     unsigned long long lifetime_ns;   // exit at a tile boundary after this long
 };
-constexpr int kServeTagShift = 24;
-constexpr uint64_t kServeMaxTiles = (1ull << kServeTagShift) - 8192;
+constexpr unsigned long long kMboxStop = 1ull << 63;
+constexpr int kMboxStride = 16;  // words between two CTAs' mailboxes (128 B)
+
+// Largest tile count of one served request (a request must fit the tile ring).
+inline uint64_t serve_max_tiles(uint64_t tile_ring) { return tile_ring / 2; }
 
 // Launch entry points implemented in the kernel translation units.  They
 // return a cudaError_t from the launch.
@@ -189,14 +202,16 @@ cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s);
 const void* batch_kernel_fn(int threads);  // for CUDA-graph kernel nodes
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s);
+cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas,
+                               cudaStream_t s);  // before each (re)launch
 cudaError_t upload_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* isb4);
 cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* sb4,
                                   const uint32_t* isb4);
 cudaError_t configure_kernels();        // bulk kernels: opt-in to large dynamic shared memory
 cudaError_t configure_batch_kernels();  // unified kernels: likewise
 
-// Unified-kernel shared memory: three table regions plus one tweak-key slot
-// (240 B, padded to 256) per warp.
-inline size_t unified_smem_bytes(int threads) { return 3 * kRegionBytes + (size_t)(threads / 32) * 256; }
+// Unified-kernel shared memory: three table regions plus one 512-B key slot
+// per warp (data schedule, then the XTS tweak schedule, 240 B each).
+inline size_t unified_smem_bytes(int threads) { return 3 * kRegionBytes + (size_t)(threads / 32) * 512; }
 
 }  // namespace kgpu

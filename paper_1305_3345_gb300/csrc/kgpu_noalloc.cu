@@ -98,7 +98,7 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
         std::lock_guard<std::mutex> lk(ctx->batch_mu);
         t = ctx->tune;
     }
-    const uint32_t threads = t.threads ? t.threads : 512;
+    const uint32_t threads = t.threads ? t.threads : 1024;
     const uint32_t tile_chunks = t.tile_chunks ? t.tile_chunks : 32;
     const uint32_t ctas = t.ctas ? t.ctas : (uint32_t)ctx->num_sms;
 

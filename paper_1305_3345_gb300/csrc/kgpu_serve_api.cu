@@ -68,7 +68,15 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     const size_t o_tstart = align_up(o_status + (size_t)S * 4, 128);
     const size_t o_tdone = o_tstart + (size_t)S * 8;
     const size_t host_bytes = o_tdone + (size_t)S * 8;
-    const size_t d_claim = 128, d_fin = d_claim + (size_t)S * 8, dev_bytes = d_fin + (size_t)S * 8;
+    // tile ring: room for every tile admission allows in flight, plus slack
+    uint64_t want = st.admit_bytes / ((uint64_t)st.tile_chunks * 512) + 2ull * S;
+    uint64_t T = 1ull << 16;
+    while (T < want && T < (1ull << 24)) T <<= 1;
+    st.tile_ring = T;
+    const size_t d_slots = sizeof(ServeDev), d_fin = d_slots + (size_t)S * sizeof(ServeSlot);
+    const size_t d_tiles = d_fin + (size_t)S * 8;
+    const size_t d_mbox = d_tiles + (size_t)T * 8;
+    const size_t dev_bytes = d_mbox + (size_t)ctx->num_sms * kMboxStride * 8;
 
     if (cudaHostAlloc(&st.host_mem, host_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
         cudaMalloc(&st.dev_mem, dev_bytes) != cudaSuccess ||
@@ -102,8 +110,13 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     a.t_start = reinterpret_cast<unsigned long long*>(dmap + o_tstart);
     a.t_done = reinterpret_cast<unsigned long long*>(dmap + o_tdone);
     a.dev = reinterpret_cast<ServeDev*>(st.dev_mem);
-    a.claim = reinterpret_cast<unsigned long long*>(st.dev_mem + d_claim);
+    a.dslots = reinterpret_cast<ServeSlot*>(st.dev_mem + d_slots);
     a.fin = reinterpret_cast<unsigned long long*>(st.dev_mem + d_fin);
+    a.tiles = reinterpret_cast<unsigned long long*>(st.dev_mem + d_tiles);
+    a.tile_mask = T - 1;
+    a.mbox = reinterpret_cast<unsigned long long*>(st.dev_mem + d_mbox);
+    a.tile_bits = 0;
+    while ((1ull << a.tile_bits) < T) a.tile_bits++;
     a.keys = ctx->d_keys;
     a.max_keys = ctx->cfg.max_keys;
     a.slot_mask = S - 1;
@@ -134,7 +147,7 @@ int ensure_running(kgpu_ctx* ctx, ServeState& st) {
     store_release(&st.hdr->stop, 0u);
     store_release(&st.hdr->exit_code, 0ull);
     DeviceGuard g(ctx->device);
-    if (cudaMemsetAsync(&reinterpret_cast<ServeDev*>(st.dev_mem)->stop, 0, sizeof(unsigned int), st.stream) !=
+    if (launch_serve_reset(reinterpret_cast<ServeDev*>(st.dev_mem), st.args.mbox, ctx->num_sms, st.stream) !=
             cudaSuccess ||
         launch_serve(st.args, 512, ctx->num_sms, st.stream) != cudaSuccess ||
         cudaEventRecord(st.kdone, st.stream) != cudaSuccess) {
@@ -168,7 +181,7 @@ int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) 
     const uint64_t len = d.nblocks * 16;
     const uint64_t units = request_units(d);
     const uint64_t nt = (units + d.tile_units - 1) / d.tile_units;
-    if (nt == 0 || nt > kServeMaxTiles) return KGPU_EINVAL;
+    if (nt == 0 || nt > serve_max_tiles(st.tile_ring)) return KGPU_EINVAL;
     const uint64_t seq = st.next_seq;
     const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
     auto refused = [&]() {
@@ -363,7 +376,7 @@ int kgpu_serve_get_stats(kgpu_ctx* ctx, kgpu_serve_stats* out) {
 }
 
 int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
-                      int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns) {
+                      int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns, uint64_t* detail) {
     if (!ctx || !reqs || !arrival_ns || !latency_ns || !n) return KGPU_EINVAL;
     std::vector<ReqDesc> descs(n);
     uint32_t tile_chunks;
@@ -408,8 +421,13 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
             for (size_t k = 0; k < pending.size(); k++) {
                 const size_t i = pending[k];
                 const uint64_t seq = seq_of[i].load(std::memory_order_acquire);
-                if (load_acquire(&st.done_seq[seq & (nslots - 1)]) >= seq + 1) {
+                const uint32_t slot = (uint32_t)(seq & (nslots - 1));
+                if (load_acquire(&st.done_seq[slot]) >= seq + 1) {
                     latency_ns[i] = t - (t0 + arrival_ns[i]);
+                    if (detail) {  // the stamps stay valid until the slot is reused
+                        detail[3 * i + 1] = load_acquire(&st.t_start[slot]);
+                        detail[3 * i + 2] = load_acquire(&st.t_done[slot]);
+                    }
                     last_done = t;
                     done++;
                 } else {
@@ -442,6 +460,7 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
                 r = publish(ctx, st, descs[i], &seq);
             }
             if (r == KGPU_OK) {
+                if (detail) detail[3 * i] = now_ns() - target;
                 seq_of[i].store(seq, std::memory_order_release);
                 produced.store(i + 1, std::memory_order_release);
                 break;

@@ -49,20 +49,32 @@ __device__ __forceinline__ void xor4(uint4& v, uint32_t a, uint32_t b, uint32_t 
     v.w ^= d;
 }
 
+// This warp's key slots in shared memory (512 B per warp after the tables):
+// the data schedule at +0 and the XTS tweak schedule at +256.
 struct WarpKeys {
-    RegKey data;          // schedule of the data cipher (encu or decu)
-    const uint32_t* twk;  // this warp's shared slot holding the tweak schedule
+    uint32_t* slot;       // generic pointer to the slot
+    uint32_t data_saddr;  // shared-window addresses for the round-key loads
+    uint32_t twk_saddr;
     int nr;
 };
+
+__device__ __forceinline__ WarpKeys warp_keys(char* smem, uint32_t warp) {
+    WarpKeys K;
+    K.slot = reinterpret_cast<uint32_t*>(smem + 3 * kRegion + warp * 512);
+    K.data_saddr = (uint32_t)__cvta_generic_to_shared(K.slot);
+    K.twk_saddr = K.data_saddr + 256;
+    K.nr = 0;
+    return K;
+}
 
 // XTS (TWEAK) or ECB over the 32-block chunks [c0, c1) of one request.
 template <bool TWEAK>
 __device__ __forceinline__ void tile_blocks(const ReqDesc& d, uint64_t c0, uint64_t c1, int dir,
                                             const WarpKeys& K) {
+    __syncwarp();  // lanes must run each step together (shuffles below)
     const uint32_t lane = lane_id();
     const UniLanes L = uni_lanes(lane, dir);
     const UniLanes LE = uni_lanes(lane, 0);
-    const SmemKey TK{K.twk};
     uint64_t blk = (c0 << 5) + lane;
     const uint32_t bps = d.unit_blocks;
     uint64_t base = 0;
@@ -75,7 +87,7 @@ __device__ __forceinline__ void tile_blocks(const ReqDesc& d, uint64_t c0, uint6
         z1 = (uint32_t)(unit >> 32);
         z2 = 0;
         z3 = 0;
-        cipher_u(z0, z1, z2, z3, TK, K.nr, LE);
+        cipher_u(z0, z1, z2, z3, K.twk_saddr, K.nr, LE);
     };
     if (TWEAK) {
         base = (c0 << 5) / bps;
@@ -89,11 +101,15 @@ __device__ __forceinline__ void tile_blocks(const ReqDesc& d, uint64_t c0, uint6
         t3 = __shfl_sync(0xffffffffu, z3, srel);
         gf128_mul_xpow(t0, t1, t2, t3, j);
     }
+    // the next chunk is fetched while this one is enciphered (one warp runs a
+    // tile alone, so the load latency would otherwise add to every step)
+    uint4 nxt = (c0 < c1 && blk < d.nblocks) ? d.src[blk] : make_uint4(0, 0, 0, 0);
     for (uint64_t c = c0; c < c1; ++c) {
         const bool valid = blk < d.nblocks;
-        uint4 v = valid ? d.src[blk] : make_uint4(0, 0, 0, 0);
+        uint4 v = nxt;
+        if (c + 1 < c1 && blk + 32 < d.nblocks) nxt = d.src[blk + 32];
         if (TWEAK) xor4(v, t0, t1, t2, t3);
-        cipher_block(v, K.data, K.nr, L, dir);
+        cipher_block(v, K.data_saddr, K.nr, L, dir);
         if (TWEAK) xor4(v, t0, t1, t2, t3);
         if (valid) d.dst[blk] = v;
         blk += 32;
@@ -132,6 +148,7 @@ __device__ __forceinline__ void tile_blocks(const ReqDesc& d, uint64_t c0, uint6
 
 // CBC decryption of pages [p0, p1) of one request (see cbc_dec_kernel).
 __device__ __forceinline__ void tile_cbc_dec(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
+    __syncwarp();
     const uint32_t lane = lane_id();
     const UniLanes L = uni_lanes(lane, 1);
     const uint32_t bpp = d.unit_blocks;
@@ -140,9 +157,11 @@ __device__ __forceinline__ void tile_cbc_dec(const ReqDesc& d, uint64_t p0, uint
     uint64_t page = p0 + lane / bpp;
     uint32_t j = lane % bpp;
     uint32_t carry0 = 0, carry1 = 0, carry2 = 0, carry3 = 0;
+    uint4 nxt = blk < bend ? d.src[blk] : make_uint4(0, 0, 0, 0);
     for (uint64_t b = p0 * bpp; b < bend; b += 32) {
         const bool valid = blk < bend;
-        const uint4 c = valid ? d.src[blk] : make_uint4(0, 0, 0, 0);
+        const uint4 c = nxt;
+        if (blk + 32 < bend) nxt = d.src[blk + 32];  // prefetch the next step
         // lane i takes lane i-1's block; lane 0 keeps lane 31's of the last step
         const uint32_t src_lane = (lane + 31) & 31;
         uint4 prev;
@@ -160,7 +179,7 @@ __device__ __forceinline__ void tile_cbc_dec(const ReqDesc& d, uint64_t p0, uint
         }
         if (valid && j == 0) prev = d.ivs[page];
         uint4 v = c;
-        cipher_block(v, K.data, K.nr, L, 1);
+        cipher_block(v, K.data_saddr, K.nr, L, 1);
         xor4(v, prev.x, prev.y, prev.z, prev.w);
         if (valid) d.dst[blk] = v;
         blk += 32;
@@ -174,22 +193,33 @@ __device__ __forceinline__ void tile_cbc_dec(const ReqDesc& d, uint64_t p0, uint
 }
 
 // CBC encryption of pages [p0, p1), p1 - p0 <= 32: one chain per lane.
+// Lanes without a page keep stepping with the others (their loads and stores
+// are predicated off), so the warp runs every chain in one converged pass.
 __device__ __forceinline__ void tile_cbc_enc(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
+    __syncwarp();
     const uint32_t lane = lane_id();
     const UniLanes L = uni_lanes(lane, 0);
     const uint64_t page = p0 + lane;
-    if (page >= p1) return;
+    const bool valid = page < p1;
     const uint32_t bpp = d.unit_blocks;
-    const uint4* in = d.src + page * bpp;
-    uint4* out = d.dst + page * bpp;
-    uint4 x = d.ivs[page];
-    uint4 nxt = in[0];
+    const uint4* in = d.src + (valid ? page : p0) * bpp;
+    uint4* out = d.dst + (valid ? page : p0) * bpp;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    uint4 x = valid ? d.ivs[page] : z;
+    // the chain is sequential, so plaintext is fetched four blocks ahead
+    uint4 q0 = valid ? in[0] : z;
+    uint4 q1 = valid && bpp > 1 ? in[1] : z;
+    uint4 q2 = valid && bpp > 2 ? in[2] : z;
+    uint4 q3 = valid && bpp > 3 ? in[3] : z;
     for (uint32_t i = 0; i < bpp; ++i) {
-        const uint4 cur = nxt;
-        if (i + 1 < bpp) nxt = in[i + 1];
+        const uint4 cur = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        if (valid && i + 4 < bpp) q3 = in[i + 4];
         xor4(x, cur.x, cur.y, cur.z, cur.w);
-        cipher_block(x, K.data, K.nr, L, 0);
-        out[i] = x;
+        cipher_block(x, K.data_saddr, K.nr, L, 0);
+        if (valid) out[i] = x;
     }
 }
 
@@ -216,14 +246,16 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
     const int dir = (d.mode == KGPU_MODE_CBC_DEC) ? 1 : (d.mode == KGPU_MODE_CBC_ENC) ? 0 : (int)d.dir;
     const uint32_t sel = d.key * 2u + (uint32_t)dir;
     if (sel != cur_sel) {
-        K.data.load(dir ? dk.decu : dk.encu);
-        K.nr = (int)dk.nr;
+        const uint32_t* sched = dir ? dk.decu : dk.encu;
+        __syncwarp();  // every lane is done with the previous key
+        K.slot[lane] = sched[lane];
+        if (lane < 28) K.slot[32 + lane] = sched[32 + lane];
         if (is_xts) {
-            uint32_t* slot = const_cast<uint32_t*>(K.twk);
-            slot[lane] = dk.twku[lane];
-            slot[lane + 32] = lane + 32 < 60 ? dk.twku[lane + 32] : 0u;
-            __syncwarp();
+            K.slot[64 + lane] = dk.twku[lane];
+            if (lane < 28) K.slot[96 + lane] = dk.twku[32 + lane];
         }
+        K.nr = (int)dk.nr;
+        __syncwarp();
         cur_sel = sel;
     }
     const uint64_t units = request_units(d);
@@ -249,9 +281,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
 
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
-    WarpKeys K;
-    K.twk = reinterpret_cast<const uint32_t*>(smem + 3 * kRegion + warp * 256);
-    K.nr = 0;
+    WarpKeys K = warp_keys(smem, warp);
     uint32_t cur_sel = 0xffffffffu;
 
     const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(a.buf);
@@ -278,15 +308,21 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
 // Serving kernel: the paper's Non-Stop Kernel (section 3.1) -- launched once,
 // fed through pinned host memory -- with every wait bounded.
 //
-// CTA 0 / warp 0 is the dispatcher: it polls the host-written request count
-// with system-scope acquire loads and mirrors it into device memory, so the
-// thousands of worker warps poll L2 instead of the host link.  Workers walk
-// the published requests in order; a request's tiles are claimed one at a time
-// with compare-and-swap on a per-slot word tagged with the request number (so
-// a warp that is late never touches the slot's next occupant), and the warp
-// that finishes the last tile publishes the completion to the host.  Requests
-// that arrive while others run are picked up as warps move past the ones that
-// are fully claimed: continuous batching at tile granularity.
+// CTA 0 / warp 0 is the dispatcher.  It polls the host-written request count
+// with system-scope acquire loads; for each new request it copies the
+// descriptor into device memory, clears the request's finish counter and
+// appends one entry per tile to a tile ring in device memory, then publishes
+// the new ring head with a release store.  Worker warps take ring positions
+// with one atomicAdd each (no retries, no contention loops), wait until their
+// position is published, run that tile and count it finished; the warp that
+// finishes a request's last tile publishes the completion to the host.  New
+// requests are appended behind whatever is running: continuous batching at
+// tile granularity.
+//
+// Exits: the host's stop flag, an idle period, or the lifetime limit make the
+// dispatcher stop publishing and raise the device stop word; workers then
+// finish any published position they hold and leave.  Positions claimed but
+// never published are handed back by serve_reset_kernel before a relaunch.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -313,70 +349,90 @@ __device__ __forceinline__ unsigned int ld_vol32(const unsigned int* p) {
 __device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-
-constexpr long long kNoTile = -1, kRetry = -2;
-
-// Claim the next tile of request r (nt tiles) from its slot word.
-__device__ long long claim_tile(unsigned long long* w, unsigned long long r, unsigned long long nt) {
-    const unsigned long long mask = (1ull << kServeTagShift) - 1;
-    unsigned long long old = ld_vol(w);
-    for (int i = 0; i < 256; i++) {
-        const unsigned long long tag = old >> kServeTagShift;
-        if (tag > r) return kNoTile;  // r is retired and its slot reused
-        unsigned long long want, k;
-        if (tag < r) {                // slot still tagged with its previous occupant
-            k = 0;
-            want = (r << kServeTagShift) | 1ull;
-        } else {
-            k = old & mask;
-            if (k >= nt) return kNoTile;
-            want = old + 1;
-        }
-        const unsigned long long prev = atomicCAS(w, old, want);
-        if (prev == old) return (long long)k;
-        old = prev;
-        __nanosleep(32);
-    }
-    return kRetry;
-}
-
-// Count one finished tile of request r; returns the finished count.
-__device__ unsigned long long finish_tile(unsigned long long* w, unsigned long long r) {
-    const unsigned long long mask = (1ull << kServeTagShift) - 1;
-    unsigned long long old = ld_vol(w);
-    for (int i = 0; i < 4096; i++) {
-        if ((old >> kServeTagShift) == r) return (atomicAdd(w, 1ull) & mask) + 1;  // tag is stable now
-        const unsigned long long prev = atomicCAS(w, old, (r << kServeTagShift) | 1ull);
-        if (prev == old) return 1;
-        old = prev;
-    }
-    return 0;  // unreachable in practice: the finish word only moves forward to r
+__device__ __forceinline__ void st_release_gpu32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
-    if (lane_id() != 0) return;
-    unsigned long long last = ld_vol(&a.dev->head);
-    unsigned long long idle_since = t0, backoff = 64;
-    unsigned int reason = 0;
+    const uint32_t lane = lane_id();
+    unsigned long long m = ld_vol(&a.dev->mirrored);   // requests enumerated so far
+    unsigned long long pub = ld_vol(&a.dev->tile_head);
+    unsigned long long idle_since = t0;
+    unsigned int backoff = 64, reason = 0;
+    const unsigned long long ring = a.tile_mask + 1;
     for (;;) {
-        const unsigned long long now = gtimer();
-        const unsigned long long h = ld_acquire_sys(&a.hh->head);
-        if (h != last) {
-            st_release_gpu(&a.dev->head, h);
-            last = h;
-            idle_since = now;
-            backoff = 64;
+        unsigned long long h = 0, now = 0;
+        unsigned int stop = 0;
+        if (lane == 0) {
+            h = ld_acquire_sys(&a.hh->head);
+            stop = *reinterpret_cast<volatile unsigned int*>(&a.hh->stop);
+            now = gtimer();
         }
-        if (ld_vol32(&a.hh->stop)) {
+        h = __shfl_sync(0xffffffffu, h, 0);
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        now = __shfl_sync(0xffffffffu, now, 0);
+        if (stop) {
             reason = kServeExitStop;
             break;
         }
+        if (m < h) {
+            // copy up to 32 new descriptors to device memory, one per lane
+            const unsigned cnt = (unsigned)(h - m < 32 ? h - m : 32);
+            unsigned long long nt = 0;
+            if (lane < cnt) {
+                const uint32_t s = (uint32_t)((m + lane) & a.slot_mask);
+                const uint4* from = reinterpret_cast<const uint4*>(&a.slots[s]);
+                uint4* to = reinterpret_cast<uint4*>(&a.dslots[s]);
+#pragma unroll
+                for (int q = 0; q < 5; q++) to[q] = from[q];  // ReqDesc, ntiles, seq
+                nt = a.dslots[s].ntiles;
+                a.fin[s] = 0;
+            }
+            // enumerate their tiles, in order, as long as the ring has room;
+            // each entry carries the high bits of its position as a tag
+            unsigned taken = 0;
+            const unsigned long long done_tiles = ld_vol(&a.dev->tile_done);
+            for (unsigned i = 0; i < cnt; i++) {
+                const unsigned long long n_i = __shfl_sync(0xffffffffu, nt, i);
+                if (pub + n_i - done_tiles > ring) break;
+                const unsigned long long s = (m + i) & a.slot_mask;
+                if (lane == i) a.dslots[s].pos0 = pub;
+                for (unsigned long long k = lane; k < n_i; k += 32) {
+                    const unsigned long long pos = pub + k;
+                    a.tiles[pos & a.tile_mask] = (((pos >> a.tile_bits) & 0xfffull) << 52) | (s << 32) | k;
+                }
+                pub += n_i;
+                taken++;
+            }
+            __syncwarp();
+            __threadfence();
+            if (taken && lane == 0) {
+                a.dev->mirrored = m + taken;
+                st_release_gpu(&a.dev->tile_head, pub);
+            }
+            if (taken) {
+                // tell every CTA through its own mailbox line: the workers
+                // poll only there, so no address is polled by the whole GPU
+                __syncwarp();
+                for (uint32_t c = lane; c < gridDim.x; c += 32)
+                    *reinterpret_cast<volatile unsigned long long*>(&a.mbox[c * kMboxStride]) = pub;
+            }
+            m += taken;
+            idle_since = now;
+            backoff = 64;
+            if (taken) continue;
+        }
         const unsigned long long done = ld_vol(&a.dev->done_count);
-        if (done != last) idle_since = now;  // requests outstanding: not idle
-        if (now - idle_since > a.idle_ns && ld_acquire_sys(&a.hh->head) == last) {
+        if (done != m || m != h) idle_since = now;  // work outstanding: not idle
+        if (now - idle_since > a.idle_ns) {
             reason = kServeExitIdle;
             break;
         }
@@ -384,13 +440,31 @@ __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
             reason = kServeExitLifetime;
             break;
         }
-        a.hh->heartbeat = now;
-        __nanosleep((unsigned)backoff);
-        if (backoff < 512) backoff <<= 1;
+        if (lane == 0) a.hh->heartbeat = now;
+        __nanosleep(backoff);
+        if (backoff < 256) backoff <<= 1;
     }
-    atomicExch(&a.dev->stop, reason);
-    a.hh->exit_code = reason;
-    __threadfence_system();
+    if (lane == 0) {
+        st_release_gpu32(&a.dev->stop, reason);
+        a.hh->exit_code = reason;
+        __threadfence_system();
+    }
+    __syncwarp();
+    for (uint32_t c = lane; c < gridDim.x; c += 32)
+        *reinterpret_cast<volatile unsigned long long*>(&a.mbox[c * kMboxStride]) = pub | kMboxStop;
+}
+
+// Before each launch: positions claimed but never published are handed back,
+// and every CTA's mailbox restarts at the published count.
+__global__ void serve_reset_kernel(ServeDev* dev, unsigned long long* mbox, int ctas) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (dev->tile_next > dev->tile_head) dev->tile_next = dev->tile_head;
+        dev->stop = 0;
+    }
+    __syncthreads();
+    const unsigned long long head = dev->tile_head;
+    for (int c = threadIdx.x; c < ctas; c += blockDim.x) mbox[c * kMboxStride] = head;
+    __threadfence();
 }
 
 template <int THREADS>
@@ -407,72 +481,85 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         serve_dispatcher(a, t0);
         return;
     }
-    WarpKeys K;
-    K.twk = reinterpret_cast<const uint32_t*>(smem + 3 * kRegion + warp * 256);
-    K.nr = 0;
+    WarpKeys K = warp_keys(smem, warp);
     uint32_t cur_sel = 0xffffffffu;
-    unsigned long long r = ld_vol(&a.dev->cursor);
-    unsigned long long idle0 = 0;
-    unsigned int backoff = 32;
-    // workers give up on their own, later than the dispatcher's idle limit,
-    // should it ever stop answering
-    const unsigned long long own_idle = a.idle_ns + 1000000000ull;
+    // a worker gives up on its own only if the dispatcher stopped answering
+    const unsigned long long own_idle = a.idle_ns + 2000000000ull;
 
+    // The loop keeps the warp's control flow uniform: lane-0-only work (the
+    // claim and the finish count) is immediately followed by a shuffle of its
+    // result, and the polling, stamps and status stores run on every lane.  A
+    // lane that branched off alone could otherwise leave the warp split into
+    // groups that then run the whole tile one after the other.
     for (;;) {
-        unsigned long long h = 0, now = 0;
-        unsigned int stop = 0;
-        if (lane == 0) {
-            h = ld_acquire_gpu(&a.dev->head);
-            stop = ld_vol32(&a.dev->stop);
-            now = gtimer();
-        }
-        h = __shfl_sync(0xffffffffu, h, 0);
-        stop = __shfl_sync(0xffffffffu, stop, 0);
-        now = __shfl_sync(0xffffffffu, now, 0);
-        if (stop || now - t0 > a.lifetime_ns) break;  // at a tile boundary: nothing held
-        if (r >= h) {
-            if (!idle0) idle0 = now;
-            else if (now - idle0 > own_idle) break;
+        unsigned long long T = 0;
+        if (lane == 0) T = atomicAdd(&a.dev->tile_next, 1ull);
+        T = __shfl_sync(0xffffffffu, T, 0);
+        // wait until position T is published (bounded: stop bit, own limit)
+        int go = 0;
+        unsigned int backoff = 32;
+        const unsigned long long w0 = gtimer();
+        const unsigned long long* box = &a.mbox[blockIdx.x * kMboxStride];
+        for (;;) {
+            // every lane reads the same word of this CTA's mailbox line
+            const unsigned long long v = __shfl_sync(0xffffffffu, ld_vol(box), 0);
+            const bool published = T < (v & ~kMboxStop);
+            if (published || (v & kMboxStop)) {
+                go = T < ld_acquire_gpu(&a.dev->tile_head) ? 1 : 0;
+                go = __shfl_sync(0xffffffffu, go, 0);
+                if (go || (v & kMboxStop)) break;
+            }
+            const unsigned long long now = __shfl_sync(0xffffffffu, gtimer(), 0);
+            if (now - w0 > own_idle) break;
             __nanosleep(backoff);
             if (backoff < 1024) backoff <<= 1;
-            unsigned long long c = lane == 0 ? ld_vol(&a.dev->cursor) : 0;
-            c = __shfl_sync(0xffffffffu, c, 0);
-            if (c > r) r = c;
-            continue;
         }
-        idle0 = 0;
-        backoff = 32;
-        const uint32_t s = (uint32_t)(r & a.slot_mask);
-        long long k = 0;
-        unsigned long long nt = 0;
-        if (lane == 0) {
-            const unsigned long long seq = ld_vol(&a.slots[s].seq);
-            nt = ld_vol(&a.slots[s].ntiles);
-            k = seq != r ? kNoTile : claim_tile(&a.claim[s], r, nt);
+        if (!go) break;
+
+        const unsigned long long e = a.tiles[T & a.tile_mask];
+        uint32_t s = (uint32_t)(e >> 32) & 0xfffffu;
+        uint64_t k = (uint32_t)e;
+        if ((e >> 52) != ((T >> a.tile_bits) & 0xfffull)) {
+            // the ring wrapped over this entry before it was read (only when
+            // many later tiles finished meanwhile): find the request that owns
+            // position T from the device copies of the in-flight descriptors
+            uint32_t found = 0xffffffffu;
+            for (uint32_t i = lane; i <= a.slot_mask; i += 32) {
+                const unsigned long long p0 = a.dslots[i].pos0, n = a.dslots[i].ntiles;
+                const unsigned long long fin = ld_vol(&a.fin[i]);
+                if (n && fin < n && T >= p0 && T < p0 + n) found = i;
+            }
+            for (int off = 16; off; off >>= 1) found = min(found, __shfl_xor_sync(0xffffffffu, found, off));
+            if (found == 0xffffffffu) continue;  // cannot happen: its request is still in flight
+            s = found;
+            k = T - a.dslots[s].pos0;
         }
-        k = __shfl_sync(0xffffffffu, k, 0);
-        nt = __shfl_sync(0xffffffffu, nt, 0);
-        if (k == kRetry) {
-            __nanosleep(128);
-            continue;
-        }
-        if (k == kNoTile) {
-            if (lane == 0) atomicMax(&a.dev->cursor, r + 1);
-            r++;
-            continue;
-        }
-        const ReqDesc d = a.slots[s].d;
-        if (k == 0 && lane == 0) a.t_start[s] = gtimer();
-        const int st = run_tile(d, (uint64_t)k, a.keys, a.max_keys, K, cur_sel);
-        if (st && lane == 0) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
+        const ReqDesc d = a.dslots[s].d;
+        const unsigned long long nt = a.dslots[s].ntiles;
+        const unsigned long long seq = a.dslots[s].seq;
+        const unsigned long long t_first = __shfl_sync(0xffffffffu, gtimer(), 0);
+        if (k == 0) a.t_start[s] = t_first;  // same value from every lane
+        const int st = run_tile(d, k, a.keys, a.max_keys, K, cur_sel);
+        if (st) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
+        // Publication: the warp barrier orders every lane's stores before
+        // lane 0, lane 0's acq_rel increment releases them at GPU scope, the
+        // last increment of a request acquires all of its tiles' stores, and
+        // the system-scope release store hands them to the host.
         __syncwarp();
-        __threadfence();  // this tile's output is visible before it is counted
-        if (lane == 0 && finish_tile(&a.fin[s], r) == nt) {
-            a.t_done[s] = gtimer();
-            __threadfence_system();
-            st_release_sys(&a.done_seq[s], r + 1);
-            atomicAdd(&a.dev->done_count, 1ull);
+        unsigned long long f = 0;
+        if (lane == 0) f = atom_add_acq_rel_gpu(&a.fin[s], 1ull) + 1;
+        f = __shfl_sync(0xffffffffu, f, 0);
+        if (f == nt) {
+            const unsigned long long t_end = __shfl_sync(0xffffffffu, gtimer(), 0);
+            if (lane == 0) {
+                a.t_done[s] = t_end;
+                st_release_sys(&a.done_seq[s], seq + 1);
+                atomicAdd(&a.dev->done_count, 1ull);
+            }
+            __syncwarp();
         }
+        if (lane == 0) atomicAdd(&a.dev->tile_done, 1ull);
+        __syncwarp();
     }
 }
 
@@ -488,21 +575,26 @@ cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, cons
 }
 
 cudaError_t configure_batch_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)unified_smem_bytes(512));
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)unified_smem_bytes(1024));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)unified_smem_bytes(512));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(serve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unified_smem_bytes(512));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)unified_smem_bytes(256));
     return e;
 }
 
 const void* batch_kernel_fn(int threads) {
+    if (threads == 1024) return reinterpret_cast<const void*>(batch_kernel<1024>);
     if (threads == 512) return reinterpret_cast<const void*>(batch_kernel<512>);
-    if (threads == 256) return reinterpret_cast<const void*>(batch_kernel<256>);
     return nullptr;
+}
+
+cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas, cudaStream_t s) {
+    serve_reset_kernel<<<1, 256, 0, s>>>(dev, mbox, ctas);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s) {
@@ -512,8 +604,8 @@ cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s) {
-    if (threads == 512) batch_kernel<512><<<grid, 512, unified_smem_bytes(512), s>>>(a);
-    else if (threads == 256) batch_kernel<256><<<grid, 256, unified_smem_bytes(256), s>>>(a);
+    if (threads == 1024) batch_kernel<1024><<<grid, 1024, unified_smem_bytes(1024), s>>>(a);
+    else if (threads == 512) batch_kernel<512><<<grid, 512, unified_smem_bytes(512), s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -117,7 +117,7 @@ def test_mixed_batch_unit_sizes(ctx, unit):
     b.close()
 
 
-@pytest.mark.parametrize("threads,tile", [(256, 1), (512, 8), (256, 128), (512, 1024)])
+@pytest.mark.parametrize("threads,tile", [(512, 1), (1024, 8), (512, 128), (1024, 1024)])
 def test_tuning_shapes_give_same_bytes(ctx, threads, tile):
     b = Batch(ctx, seed=47, n=60, lo=4096, hi=512 << 10, nkeys=8)
     ctx.set_tuning(threads, tile, 0)
@@ -188,7 +188,7 @@ def test_ticket_rotation(ctx):
 def test_autotune_picks_a_valid_shape(ctx):
     b = Batch(ctx, seed=67, n=200, lo=4096, hi=1 << 20, nkeys=16)
     best, ms = ctx.autotune(b.reqs, iters=2)
-    assert best["threads"] in (256, 512) and best["tile_chunks"] >= 1 and ms > 0
+    assert best["threads"] in (512, 1024) and best["tile_chunks"] >= 1 and ms > 0
     assert ctx.get_tuning() == best
     b.dst.zero_()
     run(ctx, b.reqs)
