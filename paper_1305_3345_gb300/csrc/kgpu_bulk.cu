@@ -122,9 +122,12 @@ __global__ void __launch_bounds__(kBulkThreads, 1) bulk_kernel(const __grid_cons
         gf128_mul_xpow(t0, t1, t2, t3, j);
     }
 
+    // the next chunk is fetched while this one is enciphered
+    uint4 nxt = blk < p.nblocks ? p.src[blk] : make_uint4(0, 0, 0, 0);
     for (uint64_t c = c0; c < c1; ++c) {
         const bool valid = blk < p.nblocks;
-        uint4 v = valid ? p.src[blk] : make_uint4(0, 0, 0, 0);
+        uint4 v = nxt;
+        if (c + 1 < c1 && blk + 32 < p.nblocks) nxt = p.src[blk + 32];
         if (TWEAK) xor4(v, t0, t1, t2, t3);
         if (DIR == 0) encrypt_block<NR>(v.x, v.y, v.z, v.w, T, K);
         else decrypt_block<NR>(v.x, v.y, v.z, v.w, T, IS, K);
@@ -194,21 +197,27 @@ __global__ void __launch_bounds__(kBulkThreads, 1) cbc_dec_kernel(const __grid_c
     uint64_t page = u0 + lane / bpp;
     uint32_t j = lane % bpp;
     uint4 carry = make_uint4(0, 0, 0, 0);
+    uint4 nxt = blk < bend ? p.src[blk] : make_uint4(0, 0, 0, 0);
 
     for (uint64_t b = u0 * bpp; b < bend; b += 32) {
         const bool valid = blk < bend;
-        const uint4 c = valid ? p.src[blk] : make_uint4(0, 0, 0, 0);
+        const uint4 c = nxt;
+        if (blk + 32 < bend) nxt = p.src[blk + 32];  // prefetch the next step
+        // one rotation gives lane i the block of lane i-1; lane 0 receives
+        // lane 31's, which it keeps for the next step and replaces by the
+        // one it kept from the previous step
+        const uint32_t from = (lane + 31) & 31;
         uint4 prev;
-        prev.x = __shfl_up_sync(0xffffffffu, c.x, 1);
-        prev.y = __shfl_up_sync(0xffffffffu, c.y, 1);
-        prev.z = __shfl_up_sync(0xffffffffu, c.z, 1);
-        prev.w = __shfl_up_sync(0xffffffffu, c.w, 1);
-        if (lane == 0) prev = carry;
+        prev.x = __shfl_sync(0xffffffffu, c.x, from);
+        prev.y = __shfl_sync(0xffffffffu, c.y, from);
+        prev.z = __shfl_sync(0xffffffffu, c.z, from);
+        prev.w = __shfl_sync(0xffffffffu, c.w, from);
+        if (lane == 0) {
+            const uint4 last = prev;
+            prev = carry;
+            carry = last;
+        }
         if (valid && j == 0) prev = p.ivs[page];
-        carry.x = __shfl_sync(0xffffffffu, c.x, 31);
-        carry.y = __shfl_sync(0xffffffffu, c.y, 31);
-        carry.z = __shfl_sync(0xffffffffu, c.z, 31);
-        carry.w = __shfl_sync(0xffffffffu, c.w, 31);
         uint4 v = c;
         decrypt_block<NR>(v.x, v.y, v.z, v.w, T, IS, K);
         xor4(v, prev.x, prev.y, prev.z, prev.w);
@@ -358,7 +367,10 @@ cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
     auto fn = cbc_fn(nr, true);
     if (!fn) return cudaErrorInvalidValue;
-    int grid = grid_for((p.npages + 31) / 32, num_sms);
+    // a 32-page group is a heavy work item (32 chains of whole pages): give
+    // every SM work as soon as there are as many groups as SMs
+    const uint64_t groups = (p.npages + 31) / 32;
+    const int grid = (int)(groups < (uint64_t)num_sms ? (groups ? groups : 1) : num_sms);
     fn<<<grid, kBulkThreads, kSmemEnc, s>>>(p);
     return cudaGetLastError();
 }
