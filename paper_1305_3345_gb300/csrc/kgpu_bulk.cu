@@ -278,6 +278,78 @@ __global__ void __launch_bounds__(kBulkThreads, 1) cbc_enc_kernel(const __grid_c
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// CBC encryption, staged.  The chains are the same (one page per lane), but a
+// lane's loads and stores at 4-KiB strides would touch 32 cache lines per
+// warp instruction; instead each warp moves 8 blocks of each of its 32 pages at
+// a time between global memory and a padded shared-memory area with
+// coalesced accesses (four 128-B lines per instruction), and the lanes read
+// and write their own chains there.  Used when a page is a multiple of 8
+// blocks (128 B).  The next 8 blocks are fetched into registers while the
+// current ones are enciphered.
+// ---------------------------------------------------------------------------
+constexpr int kStageBlocks = 8;
+constexpr int kStageRow = kStageBlocks * 16 + 16;  // one page's 8 blocks, padded against bank conflicts
+constexpr int kStageWarpBytes = 32 * kStageRow;
+
+template <int NR>
+__global__ void __launch_bounds__(kCbcEncStagedThreads, 1) cbc_enc_staged_kernel(const __grid_constant__ CbcParams p) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;
+    fill_enc(smem);
+    __syncthreads();
+
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    const Rep4 T{lane * 4u, lane * 4u + 128u};
+    const ParamKey K{p.rk};
+    const uint32_t bpp = p.bpp;
+    const uint32_t nchunks = bpp / kStageBlocks;
+    char* stage = smem + kSmemEnc + warp * kStageWarpBytes;
+    char* own = stage + lane * kStageRow;            // this lane's chain
+    const uint32_t cp_page = lane >> 3, cp_blk = lane & 7;  // coalesced copy position
+    const uint64_t ngroups = (p.npages + 31) >> 5;
+
+    for (uint64_t g = interleaved_warp(); g < ngroups; g += total_warps()) {
+        const uint64_t page = (g << 5) + lane;
+        const bool valid = page < p.npages;
+        uint4 x = valid ? p.ivs[page] : make_uint4(0, 0, 0, 0);
+        uint4 R[4 * 2];
+        auto fetch = [&](uint32_t c) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint64_t pg = (g << 5) + q * 4 + cp_page;
+                R[q] = pg < p.npages ? p.src[pg * bpp + c * kStageBlocks + cp_blk] : make_uint4(0, 0, 0, 0);
+            }
+        };
+        fetch(0);
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            __syncwarp();  // the previous chunk's ciphertext has been written out
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                *reinterpret_cast<uint4*>(stage + (q * 4 + cp_page) * kStageRow + cp_blk * 16) = R[q];
+            __syncwarp();
+            if (c + 1 < nchunks) fetch(c + 1);
+#pragma unroll 1
+            for (int i = 0; i < kStageBlocks; i++) {
+                const uint4 pt = *reinterpret_cast<const uint4*>(own + i * 16);
+                xor4(x, pt.x, pt.y, pt.z, pt.w);
+                encrypt_block<NR>(x.x, x.y, x.z, x.w, T, K);
+                *reinterpret_cast<uint4*>(own + i * 16) = x;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint64_t pg = (g << 5) + q * 4 + cp_page;
+                if (pg < p.npages)
+                    p.dst[pg * bpp + c * kStageBlocks + cp_blk] =
+                        *reinterpret_cast<const uint4*>(stage + (q * 4 + cp_page) * kStageRow + cp_blk * 16);
+            }
+        }
+    }
+}
+
 template <class P>
 using KernelFn = void (*)(P);
 
@@ -300,6 +372,15 @@ KernelFn<BulkParams> bulk_fn(int nr, int dir, bool tweak) {
         case 10: return pick_bulk<10>(dir, tweak);
         case 12: return pick_bulk<12>(dir, tweak);
         case 14: return pick_bulk<14>(dir, tweak);
+        default: return nullptr;
+    }
+}
+
+KernelFn<CbcParams> cbc_enc_staged_fn(int nr) {
+    switch (nr) {
+        case 10: return cbc_enc_staged_kernel<10>;
+        case 12: return cbc_enc_staged_kernel<12>;
+        case 14: return cbc_enc_staged_kernel<14>;
         default: return nullptr;
     }
 }
@@ -328,6 +409,9 @@ cudaError_t configure_kernels() {
                                              (int)kSmemEnc);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(cbc_fn(nr, false), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemDec);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(cbc_enc_staged_fn(nr), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemEncStaged);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -365,6 +449,14 @@ cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t
 }
 
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
+    if (p.bpp % kStageBlocks == 0) {
+        auto fn = cbc_enc_staged_fn(nr);
+        if (!fn) return cudaErrorInvalidValue;
+        const uint64_t groups = (p.npages + 31) / 32;
+        const int grid = (int)(groups < (uint64_t)num_sms ? (groups ? groups : 1) : num_sms);
+        fn<<<grid, kCbcEncStagedThreads, kSmemEncStaged, s>>>(p);
+        return cudaGetLastError();
+    }
     auto fn = cbc_fn(nr, true);
     if (!fn) return cudaErrorInvalidValue;
     // a 32-page group is a heavy work item (32 chains of whole pages): give

@@ -21,6 +21,11 @@ constexpr size_t kSmemDec = 3 * kRegionBytes;  // regions A, B, C
 // Threads per CTA of the bulk kernels (one CTA per SM).
 constexpr int kBulkThreads = 1024;
 
+// Staged CBC encryption: 16 warps per CTA, each with a 32-page x 8-block
+// staging area (4608 B) after the two table regions.
+constexpr int kCbcEncStagedThreads = 512;
+constexpr size_t kSmemEncStaged = kSmemEnc + (kCbcEncStagedThreads / 32) * 4608;
+
 // Where dynamic shared memory starts in a CTA's shared window (the reserved
 // system area comes first); the kernels fold it into their load offsets.
 constexpr int kSmemReservedBytes = 1024;
