@@ -122,13 +122,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# The sources the bulk XTS kernel is compiled from (its kernels, the device
+# cipher and the shared parameter structs); a traffic record is valid only for
+# the kernel built from exactly these bytes.
+BULK_KERNEL_SOURCES = ("aes_device.cuh", "kgpu_bulk.cu", "kgpu_internal.h")
+
+
 def csrc_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1305_3345_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(fn.encode())
-            h.update(open(os.path.join(d, fn), "rb").read())
+    for fn in BULK_KERNEL_SOURCES:
+        h.update(fn.encode())
+        h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()
 
 
