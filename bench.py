@@ -304,16 +304,26 @@ def run_batched(ctx, kg, dev):
     return out
 
 
-def run_serving(ctx, kg, dev, seconds):
+def run_serving(ctx, kg, dev, seconds, host=False):
     """Poisson arrivals at 10k..1M requests/s, sizes log-uniform 4 KiB..1 MiB,
     1,024 keys, admission cap 8 GiB in flight: the serving ring vs one launch
-    per request on the same trace (open loop, latency from arrival)."""
+    per request on the same trace (open loop, latency from arrival).  host:
+    the payload pools, outputs and IVs are registered pinned host memory that
+    the kernels read and write over the host link (the host-resident variant)."""
     import torch
     nkeys = 1024
     pool_in, pool_out = GIB, 9 * GIB
-    src = torch.from_numpy(w.seeded_bytes(5, w.STREAM_DATA, pool_in)).to(f"cuda:{dev}")
-    dst = torch.empty(pool_out, dtype=torch.uint8, device=f"cuda:{dev}")
-    ivs = torch.from_numpy(w.page_ivs(5, 1 << 20).reshape(-1).copy()).to(f"cuda:{dev}")
+    if host:
+        src = torch.empty(pool_in, dtype=torch.uint8, pin_memory=True)
+        src.copy_(torch.from_numpy(w.seeded_bytes(5, w.STREAM_DATA, pool_in)))
+        dst = torch.empty(pool_out, dtype=torch.uint8, pin_memory=True)
+        ivs = torch.from_numpy(w.page_ivs(5, 1 << 20).reshape(-1).copy()).pin_memory()
+        for b in (src, dst, ivs):
+            ctx.host_register(b)
+    else:
+        src = torch.from_numpy(w.seeded_bytes(5, w.STREAM_DATA, pool_in)).to(f"cuda:{dev}")
+        dst = torch.empty(pool_out, dtype=torch.uint8, device=f"cuda:{dev}")
+        ivs = torch.from_numpy(w.page_ivs(5, 1 << 20).reshape(-1).copy()).to(f"cuda:{dev}")
     key_mix = w.request_mix(5, 16, 4096, 1 << 20, nkeys)
     hx, hs = register_mix_keys(ctx, 5, key_mix)
     torch.cuda.synchronize()
@@ -323,6 +333,9 @@ def run_serving(ctx, kg, dev, seconds):
         mix = w.request_mix(5 + rate, n, 4096, 1 << 20, nkeys)
         mix.key_bits = key_mix.key_bits
         reqs = build_requests(kg, mix, hx, hs, src, pool_in, dst, pool_out, ivs, 5 + rate)
+        if host:
+            reqs["flags"] = np.where(mix.modes == w.MODE_XTS, kg.REQ_SRC_HOST | kg.REQ_DST_HOST,
+                                     kg.REQ_SRC_HOST | kg.REQ_DST_HOST | kg.REQ_IVS_HOST)
         arr = (w.poisson_arrivals(5 + rate, n, float(rate)) * 1e9).astype(np.uint64)
         detail = np.zeros(3 * n, dtype=np.uint64)
         ctx.serve_start(admit_bytes=8 * GIB)
@@ -356,11 +369,16 @@ def run_serving(ctx, kg, dev, seconds):
         })
     for h in list(hx) + list(hs):
         ctx.delkey(int(h))
+    if host:
+        for b in (src, dst, ivs):
+            ctx.host_unregister(b)
     del src, dst, ivs
     torch.cuda.empty_cache()
+    where = ("payloads, outputs and IVs in registered pinned host memory, read and written by the kernels "
+             "over the host link" if host else "payloads pre-staged in device memory")
     return {"workload": "Poisson arrivals, sizes 4 KiB..1 MiB log-uniform, 1024 keys (AES-128/256), "
                         "50% XTS / 25% CBC-dec / 25% CBC-enc, admission cap 8 GiB, "
-                        f"{seconds:g} s per rate",
+                        f"{seconds:g} s per rate; {where}",
             "rates": res}
 
 
@@ -407,11 +425,39 @@ def run_host_stream(ctx, kg, kh, dev):
             hs, hd = h[:size], h2[:size]
             t = timed(lambda: ctx.xts_crypt_host(kh, 0, hs, hd, SECTOR, 0, chunk), reps=3)
             out["sweep"].append({"bytes": size, "chunk": chunk, "GB/s": size / t / 1e9})
+    # zero-copy: one batched request whose pages stay in registered host
+    # memory; the kernel reads and writes them over the host link directly
+    def host_request(a, b, size):
+        r = np.zeros(1, dtype=kg.request_dtype())
+        r["mode"], r["key"], r["src"], r["dst"] = kg.MODE_XTS, kh, a.data_ptr(), b.data_ptr()
+        r["len"], r["unit_size"], r["flags"] = size, SECTOR, kg.REQ_SRC_HOST | kg.REQ_DST_HOST
+        return r
+
+    out["zero_copy"] = []
+    ctx.host_register(h)
+    ctx.host_register(h2)
+    try:
+        for size in (64 << 20, GIB):
+            r = host_request(h, h2, size)
+            t = timed(lambda: ctx.poll(ctx.submit(r), -1), reps=3)
+            out["zero_copy"].append({"bytes": size, "GB/s": size / t / 1e9})
+    finally:
+        ctx.host_unregister(h)
+        ctx.host_unregister(h2)
     del h, h2
     h4 = torch.empty(4 * GIB, dtype=torch.uint8).pin_memory()
     t = timed(lambda: ctx.xts_crypt_host(kh, 0, h4, h4, SECTOR, 0, 64 << 20), reps=2)
     out["sweep"].append({"bytes": 4 * GIB, "chunk": 64 << 20, "GB/s": 4 * GIB / t / 1e9, "in_place": True})
+    ctx.host_register(h4)
+    try:
+        r = host_request(h4, h4, 4 * GIB)
+        t = timed(lambda: ctx.poll(ctx.submit(r), -1), reps=2)
+        out["zero_copy"].append({"bytes": 4 * GIB, "GB/s": 4 * GIB / t / 1e9, "in_place": True})
+    finally:
+        ctx.host_unregister(h4)
     del h4
+    zbest = max(out["zero_copy"], key=lambda r: r["GB/s"])
+    out["zero_copy_frac_of_link_both_directions"] = 2 * zbest["GB/s"] / out["link"]["both_directions_GB/s"]
     best = max(out["sweep"], key=lambda r: r["GB/s"])
     out["best"] = best
     out["frac_of_link_both_directions"] = 2 * best["GB/s"] / out["link"]["both_directions_GB/s"]
@@ -445,9 +491,29 @@ def run_roundtrip(ctx, kg, dev):
     finally:
         ctx.serve_stop(10_000_000_000)
     rc2, lat2, _ = ctx.replay_launches(r, arr, nstreams=1)
+    # the same with the 4 KiB pages in registered host memory: the kernel
+    # reads the input and writes the output over the host link
+    hsrc = src.cpu().pin_memory()
+    hdst = torch.empty_like(hsrc).pin_memory()
+    ctx.host_register(hsrc)
+    ctx.host_register(hdst)
+    rh = r.copy()
+    rh["src"] = hsrc.data_ptr() + 4096 * np.arange(n)
+    rh["dst"] = hdst.data_ptr() + 4096 * np.arange(n)
+    rh["flags"] = kg.REQ_SRC_HOST | kg.REQ_DST_HOST
+    ctx.serve_start()
+    try:
+        rc3, lat3, _ = ctx.replay_serve(rh, arr)
+    finally:
+        ctx.serve_stop(10_000_000_000)
+    rc4, lat4, _ = ctx.replay_launches(rh, arr, nstreams=1)
+    ctx.host_unregister(hsrc)
+    ctx.host_unregister(hdst)
     ctx.delkey(key)
-    return {"workload": "4 KiB AES-256-XTS requests, one in flight at a time, 2000 requests",
+    return {"workload": "4 KiB AES-256-XTS requests, one in flight at a time, 2000 requests; "
+                        "pages in device memory, and in registered pinned host memory (host_*)",
             "ring": {"rc": rc, "latency": pct(lat)}, "launch": {"rc": rc2, "latency": pct(lat2)},
+            "host_ring": {"rc": rc3, "latency": pct(lat3)}, "host_launch": {"rc": rc4, "latency": pct(lat4)},
             "paper_context": "GTX 480 Non-Stop Kernel: 16.7 us (512 threads) for launch + 4 KB + wait"}
 
 
@@ -612,6 +678,7 @@ def run_kgpu(args):
 
     if rank == 0 and not args.no_serve and nbytes == GIB:
         line["serving"] = run_serving(ctx, kg, dev, args.serve_seconds)
+        line["serving_host"] = run_serving(ctx, kg, dev, args.serve_seconds, host=True)
         line["roundtrip"] = run_roundtrip(ctx, kg, dev)
 
     if rank == 0 and not args.no_host and nbytes == GIB:

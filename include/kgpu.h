@@ -169,12 +169,56 @@ int kgpu_aes_xts_crypt_host(kgpu_ctx *ctx, kgpu_key key, int dir, const void *sr
  * by busy-waiting on the response queue), with many requests per submission.
  * ---------------------------------------------------------------------- */
 
-/* One request of a batch.  All pointers are DEVICE pointers. */
+/*
+ * Registered host memory.  A GB300's GPU reaches page-locked host memory
+ * coherently over its NVLink-C2C link, so the batched and serving kernels can
+ * read a request's input pages from host memory and write its output pages
+ * back there directly, with no staging copy (the role of the paper's
+ * helper-driven copies in and out of pinned buffers, section 3.2).  A host
+ * range must be registered first, so that the library only ever hands the GPU
+ * host addresses it knows to be mapped for it.
+ *
+ * kgpu_host_register: ptr/len is the range (any alignment; requests inside it
+ * still need 16-byte aligned pointers).  flags:
+ *   KGPU_HOSTREG_PIN     the library page-locks and maps the range
+ *                        (cudaHostRegister) and unlocks it again on
+ *                        kgpu_host_unregister or kgpu_destroy;
+ *   KGPU_HOSTREG_PINNED  the caller has page-locked it already (cudaHostAlloc,
+ *                        cudaHostRegister, a framework's pinned allocator);
+ *                        every page of the range is checked to be pinned and
+ *                        mapped for this context's device, with one
+ *                        device-address offset for the whole range.
+ * Errors: KGPU_EINVAL (NULL, empty, wrapping, unknown flag, or overlapping a
+ * range already registered), KGPU_EFAULT (PINNED and some page is not pinned
+ * and mapped), KGPU_ENOMEM / KGPU_EIO (PIN and the runtime refused).
+ * Registration is per context; the caller keeps ownership of the memory.
+ *
+ * kgpu_host_unregister: ptr is the start of a registered range (else
+ * KGPU_ENOENT).  Waits for batches submitted with kgpu_submit and for
+ * requests published to the serving ring, then forgets the range.  Work the
+ * caller launched with kgpu_submit_noalloc runs on the caller's stream: the
+ * caller must have synchronized that stream first.
+ */
+#define KGPU_HOSTREG_PIN 0u
+#define KGPU_HOSTREG_PINNED 1u
+int kgpu_host_register(kgpu_ctx *ctx, void *ptr, size_t len, uint32_t flags);
+int kgpu_host_unregister(kgpu_ctx *ctx, void *ptr);
+
+/* kgpu_request.flags: which pointers of the request lie in registered host
+ * memory (each must then fall inside one range registered with
+ * kgpu_host_register, else KGPU_EFAULT); the others are device memory of the
+ * context's GPU.  Any other bit set: KGPU_EINVAL. */
+#define KGPU_REQ_SRC_HOST 0x1u
+#define KGPU_REQ_DST_HOST 0x2u
+#define KGPU_REQ_IVS_HOST 0x4u
+
+/* One request of a batch.  Pointers are DEVICE pointers unless flags mark
+ * them as registered host memory. */
 typedef struct kgpu_request {
     uint32_t mode;       /* KGPU_MODE_* */
     uint32_t dir;        /* KGPU_ENCRYPT / KGPU_DECRYPT for XTS and ECB; ignored for CBC */
     kgpu_key key;        /* an XTS key for KGPU_MODE_XTS, a single key otherwise */
-    uint32_t flags;      /* must be 0 */
+    uint32_t flags;      /* KGPU_REQ_* bits, or 0 */
     const void *src;     /* 16-byte aligned */
     void *dst;           /* == src (in place) or disjoint from it */
     uint64_t len;        /* bytes: a multiple of unit_size (ECB: of 16) */

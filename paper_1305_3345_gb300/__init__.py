@@ -137,6 +137,8 @@ def lib() -> ctypes.CDLL:
                 "kgpu_replay_serve": ([vp, vp, vp, sz, ctypes.c_int64, vp, ctypes.POINTER(u64), vp], i32),
                 "kgpu_replay_launches": ([vp, vp, vp, sz, u32, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
                 "kgpu_submit_noalloc": ([vp, vp, sz, vp, vp], i32),
+                "kgpu_host_register": ([vp, vp, sz, u32], i32),
+                "kgpu_host_unregister": ([vp, vp], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -334,6 +336,37 @@ def kgpu_submit_noalloc(ctx, reqs, stream=None, status=None) -> None:
     _check(rc, "kgpu_submit_noalloc")
 
 
+HOSTREG_PIN = 0
+HOSTREG_PINNED = 1
+REQ_SRC_HOST = 0x1
+REQ_DST_HOST = 0x2
+REQ_IVS_HOST = 0x4
+
+
+def _host_span(buf, nbytes=None):
+    """(address, bytes) of a host buffer: a CPU tensor, a numpy array, or an
+    integer address with nbytes."""
+    if isinstance(buf, int):
+        if nbytes is None:
+            raise ValueError("an address needs nbytes")
+        return buf, int(nbytes)
+    if hasattr(buf, "data_ptr"):
+        if buf.is_cuda:
+            raise ValueError("host registration takes host memory")
+        return buf.data_ptr(), buf.numel() * buf.element_size()
+    return buf.ctypes.data, buf.nbytes
+
+
+def kgpu_host_register(ctx, buf, nbytes=None, flags=HOSTREG_PINNED) -> None:
+    ptr, n = _host_span(buf, nbytes)
+    _check(lib().kgpu_host_register(ctx, ptr, n, flags), "kgpu_host_register")
+
+
+def kgpu_host_unregister(ctx, buf) -> None:
+    ptr = buf if isinstance(buf, int) else _host_span(buf)[0]
+    _check(lib().kgpu_host_unregister(ctx, ptr), "kgpu_host_unregister")
+
+
 def kgpu_serve_start(ctx, ring_slots=0, tile_chunks=0, admit_bytes=0, idle_timeout_ns=0, lifetime_ns=0) -> None:
     cfg = KgpuServeConfig(ring_slots, tile_chunks, admit_bytes, idle_timeout_ns, lifetime_ns)
     _check(lib().kgpu_serve_start(ctx, ctypes.byref(cfg)), "kgpu_serve_start")
@@ -469,6 +502,12 @@ class Context:
 
     def submit_noalloc(self, reqs, stream=None, status=None):
         kgpu_submit_noalloc(self.handle, reqs, stream, status)
+
+    def host_register(self, buf, nbytes=None, flags=HOSTREG_PINNED):
+        kgpu_host_register(self.handle, buf, nbytes, flags)
+
+    def host_unregister(self, buf):
+        kgpu_host_unregister(self.handle, buf)
 
     def serve_start(self, **kw):
         kgpu_serve_start(self.handle, **kw)

@@ -3,6 +3,7 @@
 // in the CUDA kernels of kgpu_bulk.cu; this file only validates and launches.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <cstring>
 #include <mutex>
@@ -100,6 +101,8 @@ int kgpu_destroy(kgpu_ctx* ctx) {
         destroy_batch_slots(ctx);
         if (ctx->key_stream) cudaStreamDestroy(ctx->key_stream);
         if (ctx->d_keys) cudaFree(ctx->d_keys);
+        for (const HostRange& r : ctx->hreg)
+            if (r.owned) cudaHostUnregister(reinterpret_cast<void*>(r.base));
     }
     delete ctx;
     return KGPU_OK;
@@ -181,6 +184,105 @@ int kgpu_aes_delkey(kgpu_ctx* ctx, kgpu_key key) {
     }
     std::memset(&ctx->keys[key - 1], 0, sizeof(HostKey));
     ctx->keys[key - 1].live = false;
+    return KGPU_OK;
+}
+
+namespace {
+
+// Every OS page of [a, e) must be page-locked host memory mapped for the
+// current device, all at one device-address offset (*off).
+int pinned_offset(uintptr_t a, uintptr_t e, intptr_t* off) {
+    long ps = sysconf(_SC_PAGESIZE);
+    const uintptr_t page = ps > 0 ? (uintptr_t)ps : 4096;
+    bool first = true;
+    for (uintptr_t p = a;;) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, reinterpret_cast<void*>(p)) != cudaSuccess) {
+            cudaGetLastError();
+            return KGPU_EFAULT;
+        }
+        if (at.type != cudaMemoryTypeHost || !at.devicePointer) return KGPU_EFAULT;
+        const intptr_t o = (intptr_t)at.devicePointer - (intptr_t)p;
+        if (first)
+            *off = o;
+        else if (o != *off)
+            return KGPU_EFAULT;
+        first = false;
+        if (p == e - 1) break;
+        const uintptr_t next = (p / page + 1) * page;
+        p = next < e ? next : e - 1;
+    }
+    return KGPU_OK;
+}
+
+}  // namespace
+
+int kgpu_host_register(kgpu_ctx* ctx, void* ptr, size_t len, uint32_t flags) {
+    if (!ctx || !ptr || !len || (flags != KGPU_HOSTREG_PIN && flags != KGPU_HOSTREG_PINNED)) return KGPU_EINVAL;
+    const uintptr_t a = (uintptr_t)ptr, e = a + len;
+    if (e < a) return KGPU_EINVAL;
+    DeviceGuard g(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->hreg_mu);
+    // the first range ending after a; ranges are disjoint, so sorted by end too
+    auto it = std::lower_bound(ctx->hreg.begin(), ctx->hreg.end(), a,
+                               [](const HostRange& r, uintptr_t x) { return r.end <= x; });
+    if (it != ctx->hreg.end() && it->base < e) return KGPU_EINVAL;
+    HostRange r;
+    r.base = a;
+    r.end = e;
+    if (flags == KGPU_HOSTREG_PIN) {
+        cudaError_t err = cudaHostRegister(ptr, len, cudaHostRegisterMapped | cudaHostRegisterPortable);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            if (err == cudaErrorHostMemoryAlreadyRegistered) return KGPU_EINVAL;
+            return err == cudaErrorMemoryAllocation ? KGPU_ENOMEM : KGPU_EIO;
+        }
+        void* dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, ptr, 0) != cudaSuccess || !dp) {
+            cudaGetLastError();
+            cudaHostUnregister(ptr);
+            return KGPU_EIO;
+        }
+        r.dev_off = (intptr_t)dp - (intptr_t)a;
+        r.owned = true;
+    } else {
+        int rc = pinned_offset(a, e, &r.dev_off);
+        if (rc) return rc;
+    }
+    ctx->hreg.insert(it, r);
+    return KGPU_OK;
+}
+
+int kgpu_host_unregister(kgpu_ctx* ctx, void* ptr) {
+    if (!ctx || !ptr) return KGPU_EINVAL;
+    auto find = [&]() {
+        return std::find_if(ctx->hreg.begin(), ctx->hreg.end(),
+                            [&](const HostRange& r) { return r.base == (uintptr_t)ptr; });
+    };
+    {
+        std::lock_guard<std::mutex> lk(ctx->hreg_mu);
+        if (find() == ctx->hreg.end()) return KGPU_ENOENT;
+    }
+    // batches in flight and requests on the serving ring may still read or
+    // write the range
+    int rc = batches_quiesce(ctx);
+    if (!rc) rc = serve_quiesce(ctx, 60000000000ll);
+    if (rc) return rc;
+    HostRange r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->hreg_mu);
+        auto it = find();
+        if (it == ctx->hreg.end()) return KGPU_ENOENT;
+        r = *it;
+        ctx->hreg.erase(it);
+    }
+    if (r.owned) {
+        DeviceGuard g(ctx->device);
+        if (cudaHostUnregister(ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return KGPU_EIO;
+        }
+    }
     return KGPU_OK;
 }
 

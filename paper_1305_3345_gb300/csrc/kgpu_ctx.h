@@ -69,6 +69,14 @@ struct ServeState {
     unsigned last_exit = 0;
 };
 
+// A host range registered with kgpu_host_register: [base, end) is page-locked
+// and mapped for the context's device, where it is seen at base + dev_off.
+struct HostRange {
+    uintptr_t base = 0, end = 0;
+    intptr_t dev_off = 0;
+    bool owned = false;  // the library page-locked it and unlocks it again
+};
+
 }  // namespace kgpu
 
 struct kgpu_ctx {
@@ -98,6 +106,10 @@ struct kgpu_ctx {
     // serving loop (kgpu_serve_*)
     std::mutex serve_mu;
     kgpu::ServeState serve;
+
+    // registered host ranges, sorted by base and disjoint
+    std::mutex hreg_mu;
+    std::vector<kgpu::HostRange> hreg;
 };
 
 
@@ -251,6 +263,33 @@ struct RangeCache {
     }
 };
 
+// [p, p + len) must lie inside one registered host range; *dev receives the
+// address the device sees for p.  Takes a lock and allocates nothing.
+inline int host_translate(kgpu_ctx* ctx, const void* p, size_t len, uintptr_t* dev) {
+    uintptr_t a = (uintptr_t)p, e = a + len;
+    if (!p || e < a) return KGPU_EFAULT;
+    std::lock_guard<std::mutex> g(ctx->hreg_mu);
+    auto it = std::upper_bound(ctx->hreg.begin(), ctx->hreg.end(), a,
+                               [](uintptr_t x, const HostRange& r) { return x < r.base; });
+    if (it == ctx->hreg.begin()) return KGPU_EFAULT;
+    --it;
+    if (a < it->base || e > it->end) return KGPU_EFAULT;
+    *dev = (uintptr_t)((intptr_t)a + it->dev_off);
+    return KGPU_OK;
+}
+
+// The device-visible address of a request buffer: device memory checked
+// through the cache, or registered host memory when `host` is set.
+template <class Cache>
+int resolve_buffer(kgpu_ctx* ctx, Cache& rc, const void* p, size_t len, bool host, uintptr_t* dev) {
+    if (host) return host_translate(ctx, p, len, dev);
+    int r = rc.check(ctx, p, len);
+    if (!r) *dev = (uintptr_t)p;
+    return r;
+}
+
+constexpr uint32_t kReqFlagsAll = KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST | KGPU_REQ_IVS_HOST;
+
 // Validate one request and write its device descriptor (tile size in 512-B
 // chunks for XTS/ECB; CBC tiles derive from it).  Cache: anything with
 // int check(const kgpu_ctx*, const void*, size_t) -- RangeCache, or a
@@ -258,7 +297,7 @@ struct RangeCache {
 template <class Cache>
 int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chunks, ReqDesc* d) {
     std::memset(d, 0, sizeof(*d));
-    if (q.flags) return KGPU_EINVAL;
+    if (q.flags & ~kReqFlagsAll) return KGPU_EINVAL;
     const bool cbc = q.mode == KGPU_MODE_CBC_DEC || q.mode == KGPU_MODE_CBC_ENC;
     const bool xts = q.mode == KGPU_MODE_XTS;
     if (!xts && !cbc && q.mode != KGPU_MODE_ECB) return KGPU_EINVAL;
@@ -275,21 +314,27 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
         const HostKey& k = ctx->keys[q.key - 1];
         if (!k.live || k.xts != xts) return KGPU_ENOENT;
     }
+    uintptr_t src = (uintptr_t)q.src, dst = (uintptr_t)q.dst, ivs = (uintptr_t)q.ivs;
     if (q.len) {
         int r = check_pair(q.src, q.dst, q.len);
         if (r) return r;
-        if ((r = rc.check(ctx, q.src, q.len)) || (r = rc.check(ctx, q.dst, q.len))) return r;
+        if ((r = resolve_buffer(ctx, rc, q.src, q.len, q.flags & KGPU_REQ_SRC_HOST, &src)) ||
+            (r = resolve_buffer(ctx, rc, q.dst, q.len, q.flags & KGPU_REQ_DST_HOST, &dst)))
+            return r;
+        // in place means the same bytes, wherever they are seen from
+        if ((src == dst) != (q.src == q.dst)) return KGPU_EINVAL;
         if (cbc) {
             uint64_t npages = q.len / unit;
             if ((uintptr_t)q.ivs & 15) return KGPU_EINVAL;
-            if ((r = rc.check(ctx, q.ivs, npages * 16))) return r;
-            uintptr_t iv0 = (uintptr_t)q.ivs, iv1 = iv0 + npages * 16, d0 = (uintptr_t)q.dst;
-            if (iv0 < d0 + q.len && d0 < iv1) return KGPU_EINVAL;
+            if ((r = resolve_buffer(ctx, rc, q.ivs, npages * 16, q.flags & KGPU_REQ_IVS_HOST, &ivs))) return r;
+            uintptr_t iv0 = ivs, iv1 = iv0 + npages * 16;
+            if (iv0 < dst + q.len && dst < iv1) return KGPU_EINVAL;
         }
+        if (src != dst && src < dst + q.len && dst < src + q.len) return KGPU_EINVAL;
     }
-    d->src = static_cast<const uint4*>(q.src);
-    d->dst = static_cast<uint4*>(q.dst);
-    d->ivs = reinterpret_cast<const uint4*>(q.ivs);
+    d->src = reinterpret_cast<const uint4*>(src);
+    d->dst = reinterpret_cast<uint4*>(dst);
+    d->ivs = reinterpret_cast<const uint4*>(ivs);
     d->nblocks = q.len / 16;
     d->first_sector = q.sector;
     d->unit_blocks = (uint32_t)(unit / 16);
