@@ -123,9 +123,9 @@ class ClockSampler:
 
 
 # The sources the bulk XTS kernel is compiled from (its kernels, the device
-# cipher and the shared parameter structs); a traffic record is valid only for
-# the kernel built from exactly these bytes.
-BULK_KERNEL_SOURCES = ("aes_device.cuh", "kgpu_bulk.cu", "kgpu_internal.h")
+# cipher and its parameter structs); a traffic record is valid only for the
+# kernel built from exactly these bytes.
+BULK_KERNEL_SOURCES = ("aes_device.cuh", "kgpu_bulk.cu", "kgpu_bulk.h")
 
 
 def csrc_hash() -> str:

@@ -77,10 +77,20 @@ void free_slot(kgpu::BatchSlot& s) {
     if (s.h_status) cudaFreeHost(s.h_status);
     if (s.d_status) cudaFree(s.d_status);
     if (s.d_counter) cudaFree(s.d_counter);
+    if (s.d_scratch) cudaFree(s.d_scratch);
     if (s.done) cudaEventDestroy(s.done);
     uint64_t gen = s.gen;
     s = kgpu::BatchSlot();
     s.gen = gen;
+}
+
+// Whether a batch holds CBC encryption of registered host pages (run through
+// the per-warp staging of the 512-thread batch kernel).
+bool needs_staging(const kgpu_request* reqs, size_t n) {
+    for (size_t i = 0; i < n; i++)
+        if (reqs[i].mode == KGPU_MODE_CBC_ENC && (reqs[i].flags & (KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST)))
+            return true;
+    return false;
 }
 
 // Grow the slot's buffers to hold n requests and (re)build its graph when the
@@ -90,6 +100,21 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
     bool rebuild = !s.exec || s.graph_threads != (int)t.threads || s.graph_grid != (int)t.ctas;
     if (!s.done && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) return KGPU_EIO;
     if (!s.d_counter && cudaMalloc(&s.d_counter, 16) != cudaSuccess) return KGPU_ENOMEM;
+    // staging scratch for every warp of the launch (at most 32 warps per SM;
+    // warps beyond it run host-page CBC encryption unstaged)
+    const uint32_t want_warps =
+        (uint32_t)std::min<uint64_t>((uint64_t)t.ctas * (t.threads / 32), (uint64_t)ctx->num_sms * 32);
+    if (s.scratch_warps < want_warps) {
+        if (s.d_scratch) cudaFree(s.d_scratch);
+        s.d_scratch = nullptr;
+        s.scratch_warps = 0;
+        if (cudaMalloc(&s.d_scratch, (size_t)want_warps * kStageWarpBytes) != cudaSuccess) {
+            cudaGetLastError();
+            return KGPU_ENOMEM;
+        }
+        s.scratch_warps = want_warps;
+        rebuild = true;
+    }
     if (s.cap < need || s.status_cap < n) {
         size_t cap = std::max(need, s.cap * 2);
         size_t scap = std::max(n, s.status_cap * 2);
@@ -129,6 +154,8 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
     s.args.max_keys = ctx->cfg.max_keys;
     s.args.next_tile = s.d_counter;
     s.args.status = s.d_status;
+    s.args.scratch = s.d_scratch;
+    s.args.scratch_warps = s.scratch_warps;
 
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return KGPU_EIO;
@@ -238,7 +265,9 @@ int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream s
     if (!ctx || !out || (n && !reqs) || n > (1u << 24)) return KGPU_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->batch_mu);
     DeviceGuard g(ctx->device);
-    const kgpu_tuning t = effective(ctx);
+    kgpu_tuning t = effective(ctx);
+    // CBC encryption of host pages is staged only in the 512-thread kernel
+    if (t.threads > 512 && needs_staging(reqs, n)) t.threads = 512;
     const uint64_t ticket = ++ctx->next_ticket;
     kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
     // rotate: the slot's previous batch must have finished before its
@@ -314,9 +343,12 @@ int kgpu_autotune(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream
     uint8_t* dbuf = nullptr;
     unsigned long long* ctr = nullptr;
     int* status = nullptr;
+    uint4* scratch = nullptr;
+    const uint32_t scratch_warps = (uint32_t)ctx->num_sms * 32;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = KGPU_OK;
     if (cudaMalloc(&dbuf, bytes) != cudaSuccess || cudaMalloc(&ctr, 16) != cudaSuccess ||
+        cudaMalloc(&scratch, (size_t)scratch_warps * kStageWarpBytes) != cudaSuccess ||
         cudaMalloc(&status, n * sizeof(int)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
@@ -339,6 +371,8 @@ int kgpu_autotune(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream
             a.max_keys = ctx->cfg.max_keys;
             a.next_tile = ctr;
             a.status = status;
+            a.scratch = scratch;
+            a.scratch_warps = scratch_warps;
             float total = 0.f;
             bool ok = true;
             for (uint32_t it = 0; it <= iters && ok; it++) {
@@ -368,6 +402,7 @@ int kgpu_autotune(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream
     if (dbuf) cudaFree(dbuf);
     if (ctr) cudaFree(ctr);
     if (status) cudaFree(status);
+    if (scratch) cudaFree(scratch);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (rc) return rc;

@@ -10,7 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "aes_device.cuh"
-#include "kgpu_internal.h"
+#include "kgpu_bulk.h"
 
 namespace kgpu {
 

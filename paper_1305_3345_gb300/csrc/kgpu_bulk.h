@@ -1,0 +1,63 @@
+// Parameter blocks and launch entry points of the bulk kernels (kgpu_bulk.cu):
+// one kernel per mode, direction and key size, for the per-call transforms.
+// Kept apart from the batched and serving formats so that the bulk kernels'
+// sources are exactly aes_device.cuh, kgpu_bulk.cu and this header.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace kgpu {
+
+constexpr int kMaxRoundKeyWords = 60;  // AES-256: 4 * (14 + 1)
+
+// Shared-memory footprint of the table layouts (see aes_device.cuh).
+constexpr size_t kRegionBytes = 65536;
+constexpr size_t kSmemEnc = 2 * kRegionBytes;  // regions A, B
+constexpr size_t kSmemDec = 3 * kRegionBytes;  // regions A, B, C
+
+// Threads per CTA of the bulk kernels (one CTA per SM).
+constexpr int kBulkThreads = 1024;
+
+// Staged CBC encryption: 16 warps per CTA, each with a 32-page x 8-block
+// staging area (4608 B) after the two table regions.
+constexpr int kCbcEncStagedThreads = 512;
+constexpr size_t kSmemEncStaged = kSmemEnc + (kCbcEncStagedThreads / 32) * 4608;
+
+// Where dynamic shared memory starts in a CTA's shared window (the reserved
+// system area comes first); the kernels fold it into their load offsets.
+constexpr int kSmemReservedBytes = 1024;
+
+// Parameters of the bulk XTS / ECB kernels (passed by value, read from the
+// constant bank).
+struct BulkParams {
+    const uint4* src;
+    uint4* dst;
+    uint64_t nblocks;       // 16-byte blocks in the buffer
+    uint32_t bps;           // blocks per data unit (XTS)
+    uint32_t pad0;
+    uint64_t first_sector;  // number of the first data unit (XTS)
+    uint32_t rk[kMaxRoundKeyWords];  // data key schedule (encryption or decryption order)
+    uint32_t tk[kMaxRoundKeyWords];  // tweak key schedule (always encryption)
+};
+
+// Parameters of the CBC kernels.
+struct CbcParams {
+    const uint4* src;
+    uint4* dst;
+    const uint4* ivs;       // one per page
+    uint64_t npages;
+    uint32_t bpp;           // blocks per page
+    uint32_t pad0;
+    uint32_t rk[kMaxRoundKeyWords];
+};
+
+cudaError_t launch_xts(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
+cudaError_t launch_ecb(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
+cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
+cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
+cudaError_t upload_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* isb4);
+cudaError_t configure_kernels();  // opt-in to large dynamic shared memory
+
+}  // namespace kgpu

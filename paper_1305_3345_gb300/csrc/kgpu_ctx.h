@@ -29,6 +29,8 @@ struct BatchSlot {
     int* h_status = nullptr;     // pinned
     size_t status_cap = 0;       // entries
     unsigned long long* d_counter = nullptr;
+    uint4* d_scratch = nullptr;  // per-warp staging for CBC encryption of host pages
+    uint32_t scratch_warps = 0;
     uint32_t nreq = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -341,6 +343,7 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
     d->key = q.key - 1;
     d->mode = q.mode;
     d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : q.dir;
+    d->host = ((q.flags & KGPU_REQ_SRC_HOST) ? kDescSrcHost : 0u) | ((q.flags & KGPU_REQ_DST_HOST) ? kDescDstHost : 0u);
     if (q.mode == KGPU_MODE_CBC_ENC) {
         d->tile_units = 32;  // one chain per lane
     } else if (q.mode == KGPU_MODE_CBC_DEC) {

@@ -8,51 +8,9 @@
 #include <cstdint>
 
 #include "kgpu.h"
+#include "kgpu_bulk.h"
 
 namespace kgpu {
-
-constexpr int kMaxRoundKeyWords = 60;  // AES-256: 4 * (14 + 1)
-
-// Shared-memory footprint of the table layouts (see aes_device.cuh).
-constexpr size_t kRegionBytes = 65536;
-constexpr size_t kSmemEnc = 2 * kRegionBytes;  // regions A, B
-constexpr size_t kSmemDec = 3 * kRegionBytes;  // regions A, B, C
-
-// Threads per CTA of the bulk kernels (one CTA per SM).
-constexpr int kBulkThreads = 1024;
-
-// Staged CBC encryption: 16 warps per CTA, each with a 32-page x 8-block
-// staging area (4608 B) after the two table regions.
-constexpr int kCbcEncStagedThreads = 512;
-constexpr size_t kSmemEncStaged = kSmemEnc + (kCbcEncStagedThreads / 32) * 4608;
-
-// Where dynamic shared memory starts in a CTA's shared window (the reserved
-// system area comes first); the kernels fold it into their load offsets.
-constexpr int kSmemReservedBytes = 1024;
-
-// Parameters of the bulk XTS / ECB kernels (passed by value, read from the
-// constant bank).
-struct BulkParams {
-    const uint4* src;
-    uint4* dst;
-    uint64_t nblocks;       // 16-byte blocks in the buffer
-    uint32_t bps;           // blocks per data unit (XTS)
-    uint32_t pad0;
-    uint64_t first_sector;  // number of the first data unit (XTS)
-    uint32_t rk[kMaxRoundKeyWords];  // data key schedule (encryption or decryption order)
-    uint32_t tk[kMaxRoundKeyWords];  // tweak key schedule (always encryption)
-};
-
-// Parameters of the CBC kernels.
-struct CbcParams {
-    const uint4* src;
-    uint4* dst;
-    const uint4* ivs;       // one per page
-    uint64_t npages;
-    uint32_t bpp;           // blocks per page
-    uint32_t pad0;
-    uint32_t rk[kMaxRoundKeyWords];
-};
 
 // Key schedules as the unified (batched / serving) kernels read them from the
 // device key table.  "u-frame" layout, 60 words each:
@@ -96,9 +54,17 @@ struct ReqDesc {
     uint32_t mode;          // KGPU_MODE_*
     uint32_t dir;           // KGPU_ENCRYPT / KGPU_DECRYPT (XTS, ECB)
     uint32_t tile_units;    // work units (32-block chunks or pages) per tile
-    uint32_t pad;
+    uint32_t host;          // kDescSrcHost | kDescDstHost: buffers in registered host memory
 };
 static_assert(sizeof(ReqDesc) == 64, "descriptor layout");
+constexpr uint32_t kDescSrcHost = 1u;
+constexpr uint32_t kDescDstHost = 2u;
+
+// Per-warp device scratch of the unified kernels: CBC encryption of
+// host-resident pages moves 8 blocks of each of a warp's 32 pages through it
+// at a time (32 x 8 x 16 B).
+constexpr uint32_t kStageBlocks = 8;
+constexpr size_t kStageWarpBytes = 32 * kStageBlocks * 16;
 
 // Work units of a request: XTS/ECB count 32-block chunks, CBC counts pages.
 __host__ __device__ inline uint64_t request_units(const ReqDesc& d) {
@@ -129,9 +95,10 @@ struct BatchArgs {
     const uint8_t* buf;  // BatchHeader | ReqDesc[nreq] | uint64_t tile_start[nreq + 1]
     const DevKey* keys;
     uint32_t max_keys;
-    uint32_t pad;
+    uint32_t scratch_warps;         // warps (by global index) that have a scratch area
     unsigned long long* next_tile;  // work counter (zero before launch)
     int* status;                    // per request: 0, or a negative KGPU_E* set by the kernel
+    uint4* scratch;                 // kStageWarpBytes per warp, or null
 };
 
 // ---------------------------------------------------------------------------
@@ -188,32 +155,28 @@ struct ServeArgs {
     uint32_t slot_mask;               // S - 1
     unsigned long long tile_mask;     // T - 1
     uint32_t tile_bits;               // log2(T)
-    uint32_t pad1;
+    uint32_t scratch_warps;           // warps (by global index) that have a scratch area
     unsigned long long idle_ns;       // exit after this long with nothing to do
     unsigned long long lifetime_ns;   // exit at a tile boundary after this long
+    uint4* scratch;                   // kStageWarpBytes per warp, or null
 };
+constexpr int kServeThreads = 512;  // threads per CTA of the serving kernel
 constexpr unsigned long long kMboxStop = 1ull << 63;
 constexpr int kMboxStride = 16;  // words between two CTAs' mailboxes (128 B)
 
 // Largest tile count of one served request (a request must fit the tile ring).
 inline uint64_t serve_max_tiles(uint64_t tile_ring) { return tile_ring / 2; }
 
-// Launch entry points implemented in the kernel translation units.  They
-// return a cudaError_t from the launch.
-cudaError_t launch_xts(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
-cudaError_t launch_ecb(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
-cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
-cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
+// Launch entry points of the unified kernels (kgpu_unified.cu).  They return
+// a cudaError_t from the launch.
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s);
 const void* batch_kernel_fn(int threads);  // for CUDA-graph kernel nodes
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s);
 cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas,
                                cudaStream_t s);  // before each (re)launch
-cudaError_t upload_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* isb4);
 cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, const uint32_t* sb4,
                                   const uint32_t* isb4);
-cudaError_t configure_kernels();        // bulk kernels: opt-in to large dynamic shared memory
-cudaError_t configure_batch_kernels();  // unified kernels: likewise
+cudaError_t configure_batch_kernels();  // unified kernels: opt-in to large dynamic shared memory
 
 // Unified-kernel shared memory: three table regions plus one 512-B key slot
 // per warp (data schedule, then the XTS tweak schedule, 240 B each).

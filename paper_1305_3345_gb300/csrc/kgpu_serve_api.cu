@@ -76,7 +76,9 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     const size_t d_slots = sizeof(ServeDev), d_fin = d_slots + (size_t)S * sizeof(ServeSlot);
     const size_t d_tiles = d_fin + (size_t)S * 8;
     const size_t d_mbox = d_tiles + (size_t)T * 8;
-    const size_t dev_bytes = d_mbox + (size_t)ctx->num_sms * kMboxStride * 8;
+    const size_t d_scratch = align_up(d_mbox + (size_t)ctx->num_sms * kMboxStride * 8, 256);
+    const uint32_t scratch_warps = (uint32_t)ctx->num_sms * (kServeThreads / 32);
+    const size_t dev_bytes = d_scratch + (size_t)scratch_warps * kStageWarpBytes;
 
     if (cudaHostAlloc(&st.host_mem, host_bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess ||
         cudaMalloc(&st.dev_mem, dev_bytes) != cudaSuccess ||
@@ -115,6 +117,8 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     a.tiles = reinterpret_cast<unsigned long long*>(st.dev_mem + d_tiles);
     a.tile_mask = T - 1;
     a.mbox = reinterpret_cast<unsigned long long*>(st.dev_mem + d_mbox);
+    a.scratch = reinterpret_cast<uint4*>(st.dev_mem + d_scratch);
+    a.scratch_warps = scratch_warps;
     a.tile_bits = 0;
     while ((1ull << a.tile_bits) < T) a.tile_bits++;
     a.keys = ctx->d_keys;
@@ -149,7 +153,7 @@ int ensure_running(kgpu_ctx* ctx, ServeState& st) {
     DeviceGuard g(ctx->device);
     if (launch_serve_reset(reinterpret_cast<ServeDev*>(st.dev_mem), st.args.mbox, ctx->num_sms, st.stream) !=
             cudaSuccess ||
-        launch_serve(st.args, 512, ctx->num_sms, st.stream) != cudaSuccess ||
+        launch_serve(st.args, kServeThreads, ctx->num_sms, st.stream) != cudaSuccess ||
         cudaEventRecord(st.kdone, st.stream) != cudaSuccess) {
         cudaGetLastError();
         return KGPU_EIO;

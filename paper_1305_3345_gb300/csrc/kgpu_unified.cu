@@ -223,6 +223,66 @@ __device__ __forceinline__ void tile_cbc_enc(const ReqDesc& d, uint64_t p0, uint
     }
 }
 
+// CBC encryption of pages in registered host memory.  Over the host link a
+// load moves a whole 128-byte line, so the one-lane-per-page accesses above
+// would carry 16 useful bytes of every 128.  Here the warp moves 8 blocks
+// (128 B) of each of its 32 pages at a time between the buffers and its
+// 4-KiB scratch area in device memory, every instruction covering four whole
+// lines, and the lanes run their chains on the scratch copy.  Scratch layout:
+// [page of the tile][block of the chunk].  Pages must hold a multiple of 8
+// blocks.  __syncwarp orders the lanes' scratch accesses (it is a memory
+// barrier among the warp's threads).
+__device__ __forceinline__ void tile_cbc_enc_staged(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K,
+                                                    uint4* stage) {
+    __syncwarp();
+    const uint32_t lane = lane_id();
+    const UniLanes L = uni_lanes(lane, 0);
+    const uint32_t bpp = d.unit_blocks;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    uint4 x = p0 + lane < p1 ? d.ivs[p0 + lane] : z;
+    const uint32_t cp_page = lane >> 3, cp_blk = lane & (kStageBlocks - 1);  // copy position
+    uint4* own = stage + lane * kStageBlocks;
+    for (uint32_t c = 0; c < bpp; c += kStageBlocks) {
+        // copy in, four instructions' worth of loads in flight at a time (the
+        // register budget of the 1024-thread kernel)
+#pragma unroll
+        for (int h = 0; h < 8; h += 4) {
+            uint4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint64_t pg = p0 + (h + q) * 4 + cp_page;
+                v[q] = pg < p1 ? d.src[pg * bpp + c + cp_blk] : z;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) stage[((h + q) * 4 + cp_page) * kStageBlocks + cp_blk] = v[q];
+        }
+        __syncwarp();
+        // the scratch copy is near (L1/L2): two blocks ahead hide its latency
+        uint4 q0 = own[0], q1 = own[1];
+#pragma unroll 1
+        for (uint32_t i = 0; i < kStageBlocks; ++i) {
+            const uint4 cur = q0;
+            q0 = q1;
+            if (i + 2 < kStageBlocks) q1 = own[i + 2];
+            xor4(x, cur.x, cur.y, cur.z, cur.w);
+            cipher_block(x, K.data_saddr, K.nr, L, 0);
+            own[i] = x;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 8; h += 4) {
+            uint4 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) v[q] = stage[((h + q) * 4 + cp_page) * kStageBlocks + cp_blk];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint64_t pg = p0 + (h + q) * 4 + cp_page;
+                if (pg < p1) d.dst[pg * bpp + c + cp_blk] = v[q];
+            }
+        }
+    }
+}
+
 // Tile t of the batch -> (request, first unit, end unit).
 __device__ __forceinline__ uint32_t find_request(const uint64_t* tile_start, uint32_t nreq, uint64_t t) {
     uint32_t lo = 0, hi = nreq;  // tile_start[lo] <= t < tile_start[hi]
@@ -235,8 +295,9 @@ __device__ __forceinline__ uint32_t find_request(const uint64_t* tile_start, uin
 }
 
 // Runs one tile of request d; returns 0 or a KGPU_E* status for the request.
+// stage: this warp's scratch area, or null.
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
-                                     WarpKeys& K, uint32_t& cur_sel) {
+                                     WarpKeys& K, uint32_t& cur_sel, uint4* stage) {
     const uint32_t lane = lane_id();
     if (d.key >= max_keys) return KGPU_ENOENT;
     const DevKey& dk = keys[d.key];
@@ -266,7 +327,12 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
         case KGPU_MODE_XTS: tile_blocks<true>(d, u0, u1, dir, K); break;
         case KGPU_MODE_ECB: tile_blocks<false>(d, u0, u1, dir, K); break;
         case KGPU_MODE_CBC_DEC: tile_cbc_dec(d, u0, u1, K); break;
-        case KGPU_MODE_CBC_ENC: tile_cbc_enc(d, u0, u1, K); break;
+        case KGPU_MODE_CBC_ENC:
+            if (stage && d.host && d.unit_blocks % kStageBlocks == 0)
+                tile_cbc_enc_staged(d, u0, u1, K, stage);
+            else
+                tile_cbc_enc(d, u0, u1, K);
+            break;
         default: return KGPU_EINVAL;
     }
     return 0;
@@ -283,6 +349,15 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
     const uint32_t warp = threadIdx.x >> 5;
     WarpKeys K = warp_keys(smem, warp);
     uint32_t cur_sel = 0xffffffffu;
+    // Staged CBC encryption of host pages is compiled into the 512-thread
+    // variant only: the 1024-thread variant has 64 registers per thread, and
+    // the staged path would make it spill (the host side runs batches that
+    // need staging with 512 threads).
+    uint4* stage = nullptr;
+    if constexpr (THREADS <= 512) {
+        const uint32_t gw = blockIdx.x * (THREADS / 32) + warp;
+        if (a.scratch && gw < a.scratch_warps) stage = a.scratch + (size_t)gw * (kStageWarpBytes / 16);
+    }
 
     const BatchHeader* hdr = reinterpret_cast<const BatchHeader*>(a.buf);
     const uint64_t total = hdr->total_tiles;
@@ -297,7 +372,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
         if (lane == 0) next = atomicAdd(a.next_tile, 1ull);  // fetched while this tile runs
         const uint32_t i = find_request(tile_start, nreq, t);
         const ReqDesc d = reqs[i];
-        const int st = run_tile(d, t - tile_start[i], a.keys, a.max_keys, K, cur_sel);
+        const int st = run_tile(d, t - tile_start[i], a.keys, a.max_keys, K, cur_sel, stage);
         if (st && lane == 0) a.status[i] = st;
         next = __shfl_sync(0xffffffffu, next, 0);
     }
@@ -483,6 +558,8 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
     }
     WarpKeys K = warp_keys(smem, warp);
     uint32_t cur_sel = 0xffffffffu;
+    const uint32_t gw = blockIdx.x * (THREADS / 32) + warp;
+    uint4* stage = a.scratch && gw < a.scratch_warps ? a.scratch + (size_t)gw * (kStageWarpBytes / 16) : nullptr;
     // a worker gives up on its own only if the dispatcher stopped answering
     const unsigned long long own_idle = a.idle_ns + 2000000000ull;
 
@@ -539,7 +616,7 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         const unsigned long long seq = a.dslots[s].seq;
         const unsigned long long t_first = __shfl_sync(0xffffffffu, gtimer(), 0);
         if (k == 0) a.t_start[s] = t_first;  // same value from every lane
-        const int st = run_tile(d, k, a.keys, a.max_keys, K, cur_sel);
+        const int st = run_tile(d, k, a.keys, a.max_keys, K, cur_sel, stage);
         if (st) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
         // Publication: the warp barrier orders every lane's stores before
         // lane 0, lane 0's acq_rel increment releases them at GPU scope, the
@@ -581,7 +658,7 @@ cudaError_t configure_batch_kernels() {
         e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unified_smem_bytes(512));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(serve_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(serve_kernel<kServeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)unified_smem_bytes(512));
     return e;
 }
@@ -598,8 +675,8 @@ cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas
 }
 
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s) {
-    if (threads != 512) return cudaErrorInvalidValue;
-    serve_kernel<512><<<grid, 512, unified_smem_bytes(512), s>>>(a);
+    if (threads != kServeThreads) return cudaErrorInvalidValue;
+    serve_kernel<kServeThreads><<<grid, kServeThreads, unified_smem_bytes(kServeThreads), s>>>(a);
     return cudaGetLastError();
 }
 

@@ -240,3 +240,39 @@ def test_host_request_errors_are_refused_before_launch(ctx):
     finally:
         ctx.host_unregister(reg)
         ctx.delkey(kh)
+
+
+@pytest.mark.parametrize("threads", [512, 1024])
+@pytest.mark.parametrize("page,npages", [(4096, 45), (512, 1025), (4112, 33), (48, 70), (128, 31)])
+def test_cbc_encrypt_of_host_pages(ctx, threads, page, npages):
+    """CBC encryption over host pages: pages of a multiple of 8 blocks go
+    through the staged (whole-line) copies, the others through direct loads;
+    ragged page counts leave part of the last 32-page tile empty."""
+    import torch
+    import paper_1305_3345_gb300 as kg
+    seed = 306 + page + npages
+    data = w.seeded_bytes(seed, w.STREAM_DATA, page * npages)
+    ivs_np = w.page_ivs(seed, npages)
+    key = w.single_key(seed, 128)
+    src, dst = pinned(data.size), pinned(data.size)
+    src.copy_(torch.from_numpy(data))
+    ivs = pinned(ivs_np.size)
+    ivs.copy_(torch.from_numpy(ivs_np.reshape(-1).copy()))
+    kh = ctx.setkey(key, False)
+    before = ctx.get_tuning()
+    for b in (src, dst, ivs):
+        ctx.host_register(b)
+    try:
+        ctx.set_tuning(threads=threads, tile_chunks=32)
+        r = np.zeros(1, dtype=kg.request_dtype())
+        r["mode"], r["key"] = w.MODE_CBC_ENC, kh
+        r["src"], r["dst"], r["ivs"] = src.data_ptr(), dst.data_ptr(), ivs.data_ptr()
+        r["len"], r["unit_size"] = data.size, page
+        r["flags"] = kg.REQ_SRC_HOST | kg.REQ_DST_HOST | kg.REQ_IVS_HOST
+        run_batch(ctx, r)
+        assert np.array_equal(dst.numpy(), oracle.cbc(key, 0, data, page, ivs_np))
+    finally:
+        ctx.set_tuning(threads=before["threads"], tile_chunks=before["tile_chunks"], ctas=before["ctas"])
+        for b in (src, dst, ivs):
+            ctx.host_unregister(b)
+        ctx.delkey(kh)
