@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sweep")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of each serving trace")
     ap.add_argument("--no-host", action="store_true", help="skip the host-resident chunk sweep")
+    ap.add_argument("--variant", default="table", choices=["table", "bitsliced"],
+                    help="cipher of the timed step: shared-memory tables (the library's bulk path) or the "
+                         "bitsliced ALU comparison variant")
     ap.add_argument("--bytes", type=int, default=GIB,
                     help="buffer size (default 1 GiB; smaller only for profiler captures)")
     return ap.parse_args()
@@ -148,6 +151,31 @@ def recorded_traffic():
     if rec.get("csrc_sha256") != csrc_hash():
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+ALU_LANE_OPS_PER_CLK_SM = 64  # LOP3 / PRMT / SHF issue rate of one SM, measured on the GB300
+BITSLICE_SOURCES = ("aes_device.cuh", "kgpu_bitslice.cu", "sbox_circuit.cuh", "kgpu_internal.h")
+
+
+def bitslice_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1305_3345_gb300", "csrc")
+    for fn in BITSLICE_SOURCES:
+        h.update(fn.encode())
+        h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()
+
+
+def recorded_bitsliced_ops():
+    """ALU lane-operations per 16-byte block of the AES-256 bitsliced kernel,
+    from the committed ncu record, if it was taken on the current sources."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "xts256_bitsliced_alu.json")))
+    except (OSError, ValueError):
+        return None
+    if rec.get("csrc_sha256") != bitslice_hash():
+        return None
+    return rec.get("alu_lane_ops_per_block")
 
 
 def measured_peaks():
@@ -553,8 +581,13 @@ def run_kgpu(args):
     src = torch.from_numpy(w.seeded_bytes(2, w.STREAM_DATA, nbytes)).to(f"cuda:{dev}")
     dst = torch.empty_like(src)
 
+    bitsliced = args.variant == "bitsliced"
+
     def step():
-        ctx.xts_crypt(kh, 0, src, dst, SECTOR, 0, stream)
+        if bitsliced:
+            ctx.xts_crypt_bitsliced(kh, 0, src, dst, SECTOR, 0, stream)
+        else:
+            ctx.xts_crypt(kh, 0, src, dst, SECTOR, 0, stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -615,6 +648,18 @@ def run_kgpu(args):
                 "peak_source": f"{props.multi_processor_count} SMs x 128 B/clk x {sm_mhz:.0f} MHz "
                                "(median SM clock sampled during the timed region)",
                 "kernel": "bulk_kernel<14,enc,xts>", "launch_ms": launch_s * 1e3}
+    if bitsliced:
+        # ALU-bound: lane-operations of the ALU pipe per block (counted once with
+        # ncu on this kernel) x blocks, against SMs x 64 lane-ops/clk x clock
+        rec = recorded_bitsliced_ops()
+        alu_peak = props.multi_processor_count * ALU_LANE_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        achieved = rec * nblocks / launch_s / 1e12 if rec else None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                    "frac": achieved / alu_peak if achieved else None, "traffic": None,
+                    "peak_source": f"{props.multi_processor_count} SMs x {ALU_LANE_OPS_PER_CLK_SM} ALU lane-ops/clk "
+                                   f"x {sm_mhz:.0f} MHz (pipe rate measured with a LOP3 probe)",
+                    "alu_lane_ops_per_block": rec,
+                    "kernel": "bs_kernel<14,xts> (+ bs_tweak_kernel)", "launch_ms": launch_s * 1e3}
     roofline_hbm = {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_hbm / hbm_peak, "traffic": traffic,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
@@ -623,10 +668,12 @@ def run_kgpu(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD if nbytes == GIB else f"AES-256-XTS encrypt, {nbytes} B (profiling case)",
+        "config": {"workload": (WORKLOAD if nbytes == GIB else f"AES-256-XTS encrypt, {nbytes} B (profiling case)")
+                   + (" -- bitsliced comparison variant" if bitsliced else ""),
                    "bytes_per_gpu": nbytes, "l2": "inputs larger than L2 (1 GiB vs 129 MB)",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks, "gpu_launches": args.steps,
+        "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks,
+        "gpu_launches": args.steps * (2 if bitsliced else 1),  # bitsliced: tweak pre-pass + cipher
     }
 
     if rank == 0 and not args.no_extra and nbytes == GIB:
@@ -642,6 +689,11 @@ def run_kgpu(args):
         specs.append(("aes128_cbc_dec_4k", lambda: ctx.cbc_decrypt(ck, src, dst, SECTOR, ivs, stream)))
         specs.append(("aes128_cbc_enc_4k", lambda: ctx.cbc_encrypt_pages(ck, src, dst, SECTOR, ivs, stream)))
         specs.append(("aes128_ecb_enc", lambda: ctx.ecb_crypt(ck, 0, src, dst, stream)))
+        # the bitsliced (ALU, no tables) comparison variant of the headline and of AES-128-XTS
+        specs.append(("aes256_xts_enc_4k_bitsliced",
+                      lambda: ctx.xts_crypt_bitsliced(kh, 0, src, dst, SECTOR, 0, stream)))
+        specs.append(("aes128_xts_enc_4k_bitsliced",
+                      lambda: ctx.xts_crypt_bitsliced(k128, 0, src, dst, SECTOR, 0, stream)))
         for name, fn in specs:
             t = time_op(fn, 20, stream)
             extra[name] = {"GB/s": GIB / t / 1e9, "ms": t * 1e3}

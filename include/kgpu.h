@@ -125,6 +125,23 @@ int kgpu_aes_xts_crypt(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, vo
                        size_t du_size, uint64_t first_sector, kgpu_stream stream);
 
 /*
+ * XTS-AES encryption by the bitsliced cipher: the comparison variant of
+ * kgpu_aes_xts_crypt, with the same arguments, layout and result bytes.  Each
+ * thread enciphers 32 blocks at once as 128 bit-planes, with the S-box as a
+ * Boolean circuit of AND/XOR gates on 32-bit words (FIPS-197 5.1.1 through
+ * composite-field inversion) and ShiftRows, MixColumns and AddRoundKey as plane
+ * renamings and XORs: no table lookups, so the work runs on the ALU instead of
+ * the shared-memory path.  The data-unit tweaks E_K2(unit) are computed by a
+ * bitsliced pre-pass into a temporary device buffer of 16 bytes per data unit,
+ * allocated and freed in stream order on `stream`.
+ * dir must be KGPU_ENCRYPT (decryption runs only on the table path):
+ * KGPU_EINVAL otherwise.  Other errors as kgpu_aes_xts_crypt, plus
+ * KGPU_ENOMEM if the tweak buffer cannot be allocated.
+ */
+int kgpu_aes_xts_crypt_bitsliced(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,
+                                 size_t du_size, uint64_t first_sector, kgpu_stream stream);
+
+/*
  * CBC decryption, one chain per page (NIST SP 800-38A 6.2):
  *   P_0 = D_K(C_0) ^ IV_page,  P_i = D_K(C_i) ^ C_{i-1}.
  * Every block is independent given C_{i-1}, so the kernel runs one block per

@@ -138,6 +138,7 @@ def lib() -> ctypes.CDLL:
                 "kgpu_replay_launches": ([vp, vp, vp, sz, u32, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
                 "kgpu_submit_noalloc": ([vp, vp, sz, vp, vp], i32),
                 "kgpu_host_register": ([vp, vp, sz, u32], i32),
+                "kgpu_aes_xts_crypt_bitsliced": ([vp, u32, i32, vp, vp, sz, sz, u64, vp], i32),
                 "kgpu_host_unregister": ([vp, vp], i32),
             }
             for name, (args, res) in sig.items():
@@ -229,6 +230,16 @@ def kgpu_aes_xts_crypt(ctx, key: int, dir: int, src, dst, du_size: int, first_se
         raise ValueError("src and dst sizes differ")
     _check(lib().kgpu_aes_xts_crypt(ctx, key, dir, sp, dp, n, du_size, first_sector, _stream(stream)),
            "kgpu_aes_xts_crypt")
+
+
+def kgpu_aes_xts_crypt_bitsliced(ctx, key: int, dir: int, src, dst, du_size: int, first_sector: int = 0,
+                                 stream=None) -> None:
+    sp, n = _dev_buf(src)
+    dp, m = _dev_buf(dst)
+    if n != m:
+        raise ValueError("src and dst sizes differ")
+    _check(lib().kgpu_aes_xts_crypt_bitsliced(ctx, key, dir, sp, dp, n, du_size, first_sector, _stream(stream)),
+           "kgpu_aes_xts_crypt_bitsliced")
 
 
 def kgpu_aes_cbc_decrypt(ctx, key: int, src, dst, page_size: int, ivs, stream=None) -> None:
@@ -472,6 +483,9 @@ class Context:
 
     def xts_crypt(self, key, dir, src, dst, du_size, first_sector=0, stream=None):
         kgpu_aes_xts_crypt(self.handle, key, dir, src, dst, du_size, first_sector, stream)
+
+    def xts_crypt_bitsliced(self, key, dir, src, dst, du_size, first_sector=0, stream=None):
+        kgpu_aes_xts_crypt_bitsliced(self.handle, key, dir, src, dst, du_size, first_sector, stream)
 
     def cbc_decrypt(self, key, src, dst, page_size, ivs, stream=None):
         kgpu_aes_cbc_decrypt(self.handle, key, src, dst, page_size, ivs, stream)

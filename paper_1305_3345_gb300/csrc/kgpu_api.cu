@@ -346,6 +346,59 @@ static int cbc_common(kgpu_ctx* ctx, kgpu_key key, bool enc, const void* src, vo
     return from_cuda(e);
 }
 
+namespace {
+
+// Plane masks of a schedule (little-endian column words): plane 32w + k of
+// round r is all ones when bit k of word w of round key r is set.
+void fill_plane_masks(uint32_t* rkm, const uint32_t* sched, int nr) {
+    for (int r = 0; r <= nr; r++)
+        for (int w = 0; w < 4; w++)
+            for (int k = 0; k < 32; k++) rkm[128 * r + 32 * w + k] = ((sched[4 * r + w] >> k) & 1u) ? ~0u : 0u;
+}
+
+}  // namespace
+
+int kgpu_aes_xts_crypt_bitsliced(kgpu_ctx* ctx, kgpu_key key, int dir, const void* src, void* dst, size_t len,
+                                 size_t du_size, uint64_t first_sector, kgpu_stream stream) {
+    int rc = xts_args(ctx, dir, len, du_size, first_sector);
+    if (rc) return rc;
+    if (dir != KGPU_ENCRYPT) return KGPU_EINVAL;
+    HostKey k;
+    if ((rc = get_key(ctx, key, true, &k))) return rc;
+    if (len == 0) return KGPU_OK;
+    if ((rc = check_pair(src, dst, len))) return rc;
+    if ((rc = check_device_range(ctx, src, len)) || (rc = check_device_range(ctx, dst, len))) return rc;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t units = len / du_size;
+    void* tw = nullptr;
+    if (cudaMallocAsync(&tw, units * 16, s) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_ENOMEM;
+    }
+    static thread_local BsParams p;  // 7.7 KB: kept off the stack
+    std::memset(&p, 0, sizeof(p));
+    p.src = static_cast<const uint4*>(src);
+    p.dst = static_cast<uint4*>(dst);
+    p.tw = static_cast<uint4*>(tw);
+    p.nblocks = len / 16;
+    p.units = units;
+    p.first_sector = first_sector;
+    p.bps = (uint32_t)(du_size / 16);
+    fill_plane_masks(p.rkm, k.twk, k.nr);
+    cudaError_t e = launch_bitsliced_tweaks(p, k.nr, ctx->num_sms, s);
+    if (e == cudaSuccess) {
+        fill_plane_masks(p.rkm, k.enc, k.nr);
+        e = launch_bitsliced(p, k.nr, true, ctx->num_sms, s);
+    }
+    cudaError_t f = cudaFreeAsync(tw, s);
+    if (e != cudaSuccess || f != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    return KGPU_OK;
+}
+
 int kgpu_aes_cbc_decrypt(kgpu_ctx* ctx, kgpu_key key, const void* src, void* dst, size_t len, size_t page_size,
                          const uint8_t* ivs, kgpu_stream stream) {
     return cbc_common(ctx, key, false, src, dst, len, page_size, ivs, stream);
