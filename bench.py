@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-requests comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop sweep")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="length of each serving trace")
+    ap.add_argument("--batch-requests", type=int, default=10000,
+                    help="requests of the batched workload (10,000; fewer for a profiling case)")
     ap.add_argument("--no-host", action="store_true", help="skip the host-resident chunk sweep")
     ap.add_argument("--variant", default="table", choices=["table", "bitsliced"],
                     help="cipher of the timed step: shared-memory tables (the library's bulk path) or the "
@@ -285,12 +287,11 @@ def build_requests(kg, mix, hx, hs, src, src_span, dst, dst_span, ivs, seed):
     return r
 
 
-def run_batched(ctx, kg, dev):
+def run_batched(ctx, kg, dev, n=10000):
     """10,000 requests, log-uniform 4 KiB..8 MiB, 256 keys (AES-128/256), modes
     50% XTS / 25% CBC-dec / 25% CBC-enc: one persistent-kernel submission
     (autotuned launch shape, CUDA-graph replay) vs one launch per request."""
     import torch
-    n = 10000
     mix = w.request_mix(4, n, 4096, 8 << 20, 256)
     hx, hs = register_mix_keys(ctx, 4, mix)
     src = torch.from_numpy(w.seeded_bytes(4, w.STREAM_DATA, GIB)).to(f"cuda:{dev}")
@@ -316,7 +317,7 @@ def run_batched(ctx, kg, dev):
     ctx.replay_launches(reqs, arr, nstreams=8)           # warm-up
     rc, lat, wall_pr = ctx.replay_launches(reqs, arr, nstreams=8)
     out = {
-        "workload": "10000 requests, 4 KiB..8 MiB log-uniform (page multiples), 256 keys, "
+        "workload": f"{n} requests, 4 KiB..8 MiB log-uniform (page multiples), 256 keys, "
                     "50% XTS / 25% CBC-dec / 25% CBC-enc, seed 4",
         "bytes": total,
         "batched": {"GB/s": total / wall / 1e9, "ms": wall * 1e3, "latency_all_requests_ms": wall * 1e3,
@@ -725,8 +726,8 @@ def run_kgpu(args):
                        "call": "kgpu_aes_xts_crypt_host (pinned host pages)"}
         del hsrc, hdst
 
-    if rank == 0 and not args.no_batched and nbytes == GIB:
-        line["batched"] = run_batched(ctx, kg, dev)
+    if rank == 0 and not args.no_batched and (nbytes == GIB or args.batch_requests != 10000):
+        line["batched"] = run_batched(ctx, kg, dev, args.batch_requests)
 
     if rank == 0 and not args.no_serve and nbytes == GIB:
         line["serving"] = run_serving(ctx, kg, dev, args.serve_seconds)

@@ -388,7 +388,7 @@ int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t
  * ---------------------------------------------------------------------- */
 
 #define KGPU_NOALLOC_MAX_REQUESTS 512
-#define KGPU_NOALLOC_SCRATCH_BYTES 40960
+#define KGPU_NOALLOC_SCRATCH_BYTES 45056
 
 /*
  * kgpu_submit for callers that cannot allocate memory when they call: for

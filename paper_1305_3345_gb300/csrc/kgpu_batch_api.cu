@@ -49,18 +49,15 @@ int pack_batch(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, uint32_t tile_
     int first = KGPU_OK;
     ReqDesc* descs = reinterpret_cast<ReqDesc*>(buf + batch_desc_offset());
     uint64_t* prefix = reinterpret_cast<uint64_t*>(buf + batch_prefix_offset((uint32_t)n));
-    uint64_t tiles = 0;
+    uint32_t* order = reinterpret_cast<uint32_t*>(buf + batch_order_offset((uint32_t)n));
     for (size_t i = 0; i < n; i++) {
         int r = make_desc(ctx, reqs[i], rc, tile_chunks, &descs[i]);
         if (req_status) req_status[i] = r;
         if (r && !first) first = r;
-        prefix[i] = tiles;
-        if (!r) {
-            uint64_t units = request_units(descs[i]);
-            tiles += (units + descs[i].tile_units - 1) / descs[i].tile_units;
-        }
+        if (r) descs[i].nblocks = 0;  // refused: no tiles
     }
-    prefix[n] = tiles;
+    const uint64_t tiles = order_batch(descs, (uint32_t)n, [&](uint32_t i) { return descs[i].nblocks == 0; },
+                                       prefix, order);
     BatchHeader* h = reinterpret_cast<BatchHeader*>(buf);
     h->total_tiles = tiles;
     h->nreq = (uint32_t)n;

@@ -356,6 +356,28 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
 }
 
 
+// Run order and tile prefix of a packed batch (descs already written; codes[i]
+// nonzero marks request i refused, which contributes no tiles).  CBC-encryption
+// requests run first: each of their tiles is 32 serial chains of a page's
+// blocks, several times longer than any other tile, and handed out last they
+// would run alone at the end of the batch (the longest-first rule for
+// scheduling independent jobs).  Returns the total tile count.
+template <class Codes>
+uint64_t order_batch(const ReqDesc* descs, uint32_t n, const Codes& codes, uint64_t* prefix, uint32_t* order) {
+    uint32_t k = 0;
+    for (uint32_t pass = 0; pass < 2; pass++)
+        for (uint32_t i = 0; i < n; i++)
+            if ((descs[i].mode == KGPU_MODE_CBC_ENC) == (pass == 0)) order[k++] = i;
+    uint64_t tiles = 0;
+    for (uint32_t j = 0; j < n; j++) {
+        const uint32_t i = order[j];
+        prefix[j] = tiles;
+        if (!codes(i)) tiles += (request_units(descs[i]) + descs[i].tile_units - 1) / descs[i].tile_units;
+    }
+    prefix[n] = tiles;
+    return tiles;
+}
+
 void destroy_batch_slots(kgpu_ctx* ctx);  // kgpu_batch_api.cu
 void destroy_serve(kgpu_ctx* ctx);        // kgpu_serve_api.cu
 // Wait until every request published to the serving ring so far has completed

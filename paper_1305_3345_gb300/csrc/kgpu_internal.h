@@ -73,20 +73,26 @@ __host__ __device__ inline uint64_t request_units(const ReqDesc& d) {
 }
 
 // Header of a batch as copied to the device: the descriptors follow, then the
-// exclusive prefix of tiles per request (nreq + 1 entries).
+// exclusive prefix of tiles per request in run order (nreq + 1 entries), then
+// the run order.
 struct BatchHeader {
     uint64_t total_tiles;
     uint32_t nreq;
     uint32_t pad;
 };
 
-// Byte layout of a batch on the device: header, descriptors, tile prefix.
+// Byte layout of a batch on the device: header, descriptors, tile prefix, run order.
 __host__ __device__ constexpr size_t batch_desc_offset() { return sizeof(BatchHeader); }
 __host__ __device__ constexpr size_t batch_prefix_offset(uint32_t nreq) {
     return sizeof(BatchHeader) + (size_t)nreq * sizeof(ReqDesc);
 }
-__host__ __device__ constexpr size_t batch_bytes(uint32_t nreq) {
+// The run order follows the prefix: order[k] is the index of the k-th request
+// whose tiles are handed out (the prefix counts tiles in run order).
+__host__ __device__ constexpr size_t batch_order_offset(uint32_t nreq) {
     return batch_prefix_offset(nreq) + ((size_t)nreq + 1) * sizeof(uint64_t);
+}
+__host__ __device__ constexpr size_t batch_bytes(uint32_t nreq) {
+    return batch_order_offset(nreq) + ((size_t)nreq * sizeof(uint32_t) + 7) / 8 * 8;
 }
 
 // Arguments of the unified batch kernel (fixed per staging slot, so a captured

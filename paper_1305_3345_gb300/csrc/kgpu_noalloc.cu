@@ -106,17 +106,15 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
     FixedRangeCache cache;
     ReqDesc* descs = reinterpret_cast<ReqDesc*>(g_pack + batch_desc_offset());
     uint64_t* prefix = reinterpret_cast<uint64_t*>(g_pack + batch_prefix_offset((uint32_t)n));
-    uint64_t tiles = 0;
+    uint32_t* order = reinterpret_cast<uint32_t*>(g_pack + batch_order_offset((uint32_t)n));
     int first = KGPU_OK;
     for (size_t i = 0; i < n; i++) {
         int r = make_desc(ctx, reqs[i], cache, tile_chunks, &descs[i]);
         if (req_status) req_status[i] = r;
         if (r && !first) first = r;
-        prefix[i] = tiles;
-        if (!r) tiles += (request_units(descs[i]) + descs[i].tile_units - 1) / descs[i].tile_units;
     }
     if (first) return first;
-    prefix[n] = tiles;
+    const uint64_t tiles = order_batch(descs, (uint32_t)n, [](uint32_t) { return false; }, prefix, order);
     BatchHeader* h = reinterpret_cast<BatchHeader*>(g_pack);
     h->total_tiles = tiles;
     h->nreq = (uint32_t)n;

@@ -364,15 +364,17 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
     const uint32_t nreq = hdr->nreq;
     const ReqDesc* reqs = reinterpret_cast<const ReqDesc*>(a.buf + batch_desc_offset());
     const uint64_t* tile_start = reinterpret_cast<const uint64_t*>(a.buf + batch_prefix_offset(nreq));
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(a.buf + batch_order_offset(nreq));
     unsigned long long next = 0;
     if (lane == 0) next = atomicAdd(a.next_tile, 1ull);
     next = __shfl_sync(0xffffffffu, next, 0);
     while (next < total) {
         const uint64_t t = next;
         if (lane == 0) next = atomicAdd(a.next_tile, 1ull);  // fetched while this tile runs
-        const uint32_t i = find_request(tile_start, nreq, t);
+        const uint32_t k = find_request(tile_start, nreq, t);
+        const uint32_t i = order[k];
         const ReqDesc d = reqs[i];
-        const int st = run_tile(d, t - tile_start[i], a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
         if (st && lane == 0) a.status[i] = st;
         next = __shfl_sync(0xffffffffu, next, 0);
     }
