@@ -340,8 +340,24 @@ typedef struct {
     uint64_t first_sector;
 } XtsJob;
 
-/* IEEE 1619 5.3.1 / 5.4.1 for data unit u: T = E_K2(i) with i the data-unit
- * number as a 128-bit little-endian value; block j uses T * alpha^j. */
+/* IEEE 1619 5.3.1 / 5.4.1 on one 16-byte block with tweak value t:
+ * out = E_K1(in ^ t) ^ t (or D_K1 for decryption). */
+static void xts_block(const XtsJob *jb, int dir, const uint8_t in[16], uint8_t out[16], const uint8_t t[16]) {
+    uint8_t pp[16], cc[16];
+    for (int k = 0; k < 16; k++) pp[k] = (uint8_t)(in[k] ^ t[k]);
+    if (dir == 0) cipher(pp, cc, &jb->k1);
+    else inv_cipher(pp, cc, &jb->k1);
+    for (int k = 0; k < 16; k++) out[k] = (uint8_t)(cc[k] ^ t[k]);
+}
+
+/* IEEE 1619 5.3 / 5.4 for data unit u: T = E_K2(i) with i the data-unit
+ * number as a 128-bit little-endian value; block j uses T * alpha^j.  A unit
+ * of m full blocks and a final partial block of b bytes (0 < b < 16) ends with
+ * ciphertext stealing (5.3.2 encryption, 5.4.2 decryption):
+ *   encryption: CC = enc(P_{m-1}, T a^{m-1}); C_m = the first b bytes of CC;
+ *               C_{m-1} = enc(P_m || the last 16-b bytes of CC, T a^m);
+ *   decryption: PP = dec(C_{m-1}, T a^m); P_m = the first b bytes of PP;
+ *               P_{m-1} = dec(C_m || the last 16-b bytes of PP, T a^{m-1}). */
 static void xts_unit(void *ctx, size_t u) {
     XtsJob *jb = (XtsJob *)ctx;
     uint64_t sector = jb->first_sector + (uint64_t)u;
@@ -349,26 +365,45 @@ static void xts_unit(void *ctx, size_t u) {
     for (int k = 0; k < 8; k++) ival[k] = (uint8_t)(sector >> (8 * k));
     uint8_t t[16];
     cipher(ival, t, &jb->k2);
-    size_t nblk = jb->du / 16;
+    const size_t m = jb->du / 16, b = jb->du % 16;
     const uint8_t *in = jb->src + u * jb->du;
     uint8_t *out = jb->dst + u * jb->du;
-    for (size_t j = 0; j < nblk; j++) {
-        uint8_t pp[16], cc[16];
-        for (int k = 0; k < 16; k++) pp[k] = (uint8_t)(in[16 * j + k] ^ t[k]);
-        if (jb->dir == 0) cipher(pp, cc, &jb->k1);
-        else inv_cipher(pp, cc, &jb->k1);
-        for (int k = 0; k < 16; k++) out[16 * j + k] = (uint8_t)(cc[k] ^ t[k]);
+    /* the blocks before the stealing pair (all of them when b == 0) */
+    const size_t plain = b ? m - 1 : m;
+    for (size_t j = 0; j < plain; j++) {
+        xts_block(jb, jb->dir, in + 16 * j, out + 16 * j, t);
         oracle_xts_mul_alpha(t);
+    }
+    if (!b) return;
+    uint8_t t_last[16], last[16], tail[16], x[16], y[16];
+    memcpy(t_last, t, 16); /* T a^{m-1} */
+    oracle_xts_mul_alpha(t_last);
+    /* now t = T a^{m-1}, t_last = T a^m; read both inputs before writing */
+    memcpy(last, in + 16 * (m - 1), 16);
+    memcpy(tail, in + 16 * m, b);
+    if (jb->dir == 0) {
+        xts_block(jb, 0, last, x, t);             /* CC */
+        memcpy(y, tail, b);                        /* PP = P_m || CC[b..16) */
+        memcpy(y + b, x + b, 16 - b);
+        xts_block(jb, 0, y, out + 16 * (m - 1), t_last);
+        memcpy(out + 16 * m, x, b);                /* C_m = CC[0..b) */
+    } else {
+        xts_block(jb, 1, last, x, t_last);        /* PP */
+        memcpy(y, tail, b);                        /* CC = C_m || PP[b..16) */
+        memcpy(y + b, x + b, 16 - b);
+        xts_block(jb, 1, y, out + 16 * (m - 1), t);
+        memcpy(out + 16 * m, x, b);                /* P_m = PP[0..b) */
     }
 }
 
 /* key = Key1 || Key2 (key_len 32 or 64 bytes), dir 0 encrypt / 1 decrypt.
- * len must be a multiple of du and du a nonzero multiple of 16 (no ciphertext
- * stealing).  Key1 == Key2 is rejected, as IEEE 1619-2018 requires. */
+ * len must be a multiple of du and du at least 16 bytes; a du that is not a
+ * multiple of 16 ends every unit with ciphertext stealing.  Key1 == Key2 is
+ * rejected, as IEEE 1619-2018 requires. */
 int oracle_xts(const uint8_t *key, int key_len, int dir, const uint8_t *src, uint8_t *dst,
                size_t len, size_t du, uint64_t first_sector, int nthreads) {
     if (key_len != 32 && key_len != 64) return OR_EINVAL;
-    if (du == 0 || du % 16 || len % du) return OR_EINVAL;
+    if (du < 16 || len % du) return OR_EINVAL;
     if (dir != 0 && dir != 1) return OR_EINVAL;
     int half = key_len / 2;
     if (memcmp(key, key + half, (size_t)half) == 0) return OR_EINVAL;

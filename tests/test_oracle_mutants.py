@@ -29,6 +29,9 @@ MUTANTS = {
     "affine_constant": ("((0x63 >> i) & 1)", "((0x62 >> i) & 1)"),
     "rcon_step": ("rcon = xtime(rcon);", "rcon = (uint8_t)(rcon + 1);"),
     "mixcol_coeff": ("oracle_gf_mul(3, a1) ^ a2 ^ a3);", "oracle_gf_mul(2, a1) ^ a2 ^ a3);"),
+    "cts_first_tweak": ("xts_block(jb, 0, last, x, t);", "xts_block(jb, 0, last, x, t_last);"),
+    "cts_second_tweak": ("xts_block(jb, 0, y, out + 16 * (m - 1), t_last);",
+                         "xts_block(jb, 0, y, out + 16 * (m - 1), t);"),
 }
 
 
@@ -61,6 +64,15 @@ def _pins_pass(lib) -> bool:
             c = Cipher(algorithms.AES(key), modes.XTS((300 + u).to_bytes(16, "little"))).encryptor()
             ref += c.update(data[u * 512:(u + 1) * 512].tobytes()) + c.finalize()
         ok &= out.tobytes() == ref
+        # ciphertext stealing: units of 2 full blocks and 1 byte
+        cts = data[: 2 * 33]
+        out2 = np.zeros_like(cts)
+        lib.oracle_xts(key, len(key), 0, cts.ctypes.data, out2.ctypes.data, cts.size, 33, 300, 1)
+        ref = b""
+        for u in range(2):
+            c = Cipher(algorithms.AES(key), modes.XTS((300 + u).to_bytes(16, "little"))).encryptor()
+            ref += c.update(cts[u * 33:(u + 1) * 33].tobytes()) + c.finalize()
+        ok &= out2.tobytes() == ref
         k1 = key[: bits // 8]
         ivs = w.page_ivs(21, 2)
         lib.oracle_cbc(k1, len(k1), 0, data.ctypes.data, out.ctypes.data, data.size, 512, ivs.ctypes.data, 1)

@@ -217,9 +217,28 @@ def test_xts_rejects():
     with pytest.raises(oracle.OracleError):
         oracle.xts(key, 0, d[:4000], 4096)              # not a whole data unit
     with pytest.raises(oracle.OracleError):
-        oracle.xts(key, 0, d, 24)                       # du not a multiple of 16
+        oracle.xts(key, 0, d, 24)                       # 4096 is not a whole number of 24-B units
+    with pytest.raises(oracle.OracleError):
+        oracle.xts(key, 0, d[:4088], 8)                 # a unit shorter than one block
     with pytest.raises(oracle.OracleError):
         oracle.xts(key[:48], 0, d, 4096)                # bad key length
+
+
+@pytest.mark.parametrize("bits", [128, 256])
+@pytest.mark.parametrize("du,first", [(17, 0), (31, 5), (33, 2**40), (100, 7), (527, 2**63 - 3), (4100, 11)])
+def test_xts_ciphertext_stealing_vs_openssl(bits, du, first):
+    """IEEE 1619 5.3.2 / 5.4.2: a unit ending in a partial block steals the tail
+    of the previous block's ciphertext; OpenSSL implements the same rule."""
+    key = w.xts_key(6, bits)
+    data = w.seeded_bytes(6 + du, w.STREAM_DATA, du * 13)
+    c = oracle.xts(key, 0, data, du, first)
+    assert c.tobytes() == _openssl_xts(key, 0, data.tobytes(), du, first)
+    assert oracle.xts(key, 1, c, du, first).tobytes() == data.tobytes()
+    assert oracle.xts(key, 1, c, du, first).tobytes() == _openssl_xts(key, 1, c.tobytes(), du, first)
+    # in place, threaded
+    buf = data.copy()
+    oracle.xts(key, 0, buf, du, first, out=buf, nthreads=5)
+    assert np.array_equal(buf, c)
 
 
 def test_xts_in_place_and_threads():
