@@ -117,8 +117,14 @@ int kgpu_aes_delkey(kgpu_ctx *ctx, kgpu_key key);
  * unit u is numbered first_sector + u, its tweak is E_Key2(number) with the
  * number as a 128-bit little-endian value, and block j of the unit is
  * processed with tweak * alpha^j in GF(2^128).  dir: KGPU_ENCRYPT / DECRYPT.
- * du_size: any nonzero multiple of 16 (512 and 4096 are the usual sectors).
- * src, dst: device pointers, len bytes each.  Async on `stream`.
+ * du_size: at least 16 bytes (512 and 4096 are the usual sectors).  A
+ * du_size that is not a multiple of 16 ends every unit with a partial block,
+ * handled by ciphertext stealing (IEEE 1619 5.3.2 / 5.4.2): the last full
+ * block and the partial block are processed together, so every unit keeps its
+ * length.  (Only this per-call entry point takes such units; the batched,
+ * serving, host-pipeline and bitsliced forms require multiples of 16.)
+ * src, dst: device pointers, len bytes each, 16-byte aligned; len a multiple
+ * of du_size.  Async on `stream`.
  * Errors: KGPU_EINVAL, KGPU_ENOENT (not an XTS key), KGPU_EFAULT, KGPU_EIO.
  */
 int kgpu_aes_xts_crypt(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,

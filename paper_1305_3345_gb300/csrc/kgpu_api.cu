@@ -288,13 +288,26 @@ int kgpu_host_unregister(kgpu_ctx* ctx, void* ptr) {
 
 int kgpu_aes_xts_crypt(kgpu_ctx* ctx, kgpu_key key, int dir, const void* src, void* dst, size_t len,
                        size_t du_size, uint64_t first_sector, kgpu_stream stream) {
-    int rc = xts_args(ctx, dir, len, du_size, first_sector);
+    int rc = xts_args(ctx, dir, len, du_size, first_sector, true);
     if (rc) return rc;
     HostKey k;
     if ((rc = get_key(ctx, key, true, &k))) return rc;
     if (len == 0) return KGPU_OK;
     if ((rc = check_pair(src, dst, len))) return rc;
     if ((rc = check_device_range(ctx, src, len)) || (rc = check_device_range(ctx, dst, len))) return rc;
+    if (du_size % 16) {  // data units ending in a partial block: ciphertext stealing
+        CtsParams c;
+        std::memset(&c, 0, sizeof(c));
+        c.src = static_cast<const uint8_t*>(src);
+        c.dst = static_cast<uint8_t*>(dst);
+        c.units = len / du_size;
+        c.du = du_size;
+        c.first_sector = first_sector;
+        std::memcpy(c.rk, dir == KGPU_ENCRYPT ? k.enc : k.dec, sizeof(c.rk));
+        std::memcpy(c.tk, k.twk, sizeof(c.tk));
+        DeviceGuard g(ctx->device);
+        return from_cuda(launch_xts_cts(c, k.nr, dir, ctx->num_sms, (cudaStream_t)stream));
+    }
     BulkParams p;
     fill_bulk(&p, k, dir, src, dst, len, du_size, first_sector);
     DeviceGuard g(ctx->device);

@@ -350,6 +350,124 @@ __global__ void __launch_bounds__(kCbcEncStagedThreads, 1) cbc_enc_staged_kernel
     }
 }
 
+// ---------------------------------------------------------------------------
+// XTS with ciphertext stealing (IEEE 1619-2007 5.3.2 encryption, 5.4.2
+// decryption) for data units of du bytes, du >= 16 and not a multiple of 16:
+// m full blocks and a final partial block of b bytes.  One warp per data unit:
+// full blocks 0..m-2 go to the lanes (block j with T * alpha^j), then lane 0
+// runs the stealing pair, the last full block and the partial block, which
+// depend on each other:
+//   encryption: CC = enc(P_{m-1}, T a^{m-1});  C_m = CC[0..b);
+//               C_{m-1} = enc(P_m || CC[b..16), T a^m)
+//   decryption: PP = dec(C_{m-1}, T a^m);  P_m = PP[0..b);
+//               P_{m-1} = dec(C_m || PP[b..16), T a^{m-1})
+// Unit starts are only as aligned as u * du, so the unit's blocks move through
+// 16-, 4- or 1-byte accesses as its start allows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 load_block(const uint8_t* q, uint32_t align) {
+    if (align == 16) return *reinterpret_cast<const uint4*>(q);
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (align == 4) {
+            w[i] = reinterpret_cast<const uint32_t*>(q)[i];
+        } else {
+            w[i] = (uint32_t)q[4 * i] | (uint32_t)q[4 * i + 1] << 8 | (uint32_t)q[4 * i + 2] << 16 |
+                   (uint32_t)q[4 * i + 3] << 24;
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ void store_block(uint8_t* q, const uint4& v, uint32_t align) {
+    if (align == 16) {
+        *reinterpret_cast<uint4*>(q) = v;
+        return;
+    }
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        if (align == 4) {
+            reinterpret_cast<uint32_t*>(q)[i] = w[i];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) q[4 * i + k] = (uint8_t)(w[i] >> (8 * k));
+        }
+    }
+}
+
+template <int NR, int DIR>
+__global__ void __launch_bounds__(kBulkThreads, 1) xts_cts_kernel(const __grid_constant__ CtsParams p) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;
+    if (DIR == 0) fill_enc(smem);
+    else fill_dec(smem);
+    __syncthreads();
+
+    const uint32_t lane = lane_id();
+    const Rep4 T{lane * 4u, lane * 4u + 128u};
+    const Rep1<2> IS{lane * 4u};
+    const Rep1<2> TE{lane * 4u + 128u};
+    const ParamKey K{p.rk};
+    const ParamKey TK{p.tk};
+    const uint64_t m = p.du / 16;
+    const uint32_t b = (uint32_t)(p.du % 16);
+
+    auto block = [&](uint4& v, uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3) {
+        xor4(v, t0, t1, t2, t3);
+        if (DIR == 0) encrypt_block<NR>(v.x, v.y, v.z, v.w, T, K);
+        else decrypt_block<NR>(v.x, v.y, v.z, v.w, T, IS, K);
+        xor4(v, t0, t1, t2, t3);
+    };
+
+    for (uint64_t u = interleaved_warp(); u < p.units; u += total_warps()) {
+        const uint8_t* in = p.src + u * p.du;
+        uint8_t* out = p.dst + u * p.du;
+        const uint32_t off = (uint32_t)((uintptr_t)in & 15u);
+        const uint32_t align = off == 0 ? 16u : (off & 3u) == 0 ? 4u : 1u;
+        // E_K2(unit number) on every lane
+        const uint64_t unit = p.first_sector + u;
+        uint32_t z0 = (uint32_t)unit, z1 = (uint32_t)(unit >> 32), z2 = 0, z3 = 0;
+        if (DIR == 0) encrypt_block<NR>(z0, z1, z2, z3, T, TK);
+        else encrypt_block<NR>(z0, z1, z2, z3, TE, TK);
+        // blocks 0..m-2, lane-strided
+        uint32_t t0 = z0, t1 = z1, t2 = z2, t3 = z3;
+        gf128_mul_xk(t0, t1, t2, t3, lane);
+        for (uint64_t j = lane; j + 1 < m; j += 32) {
+            uint4 v = load_block(in + 16 * j, align);
+            block(v, t0, t1, t2, t3);
+            store_block(out + 16 * j, v, align);
+            gf128_mul_x32(t0, t1, t2, t3);
+        }
+        // the stealing pair: tweaks T a^{m-1} (a*) and T a^m (c*)
+        if (lane == 0) {
+            uint32_t a0 = z0, a1 = z1, a2 = z2, a3 = z3;
+            gf128_mul_xpow(a0, a1, a2, a3, (uint32_t)(m - 1));
+            uint32_t c0 = a0, c1 = a1, c2 = a2, c3 = a3;
+            gf128_mul_xk(c0, c1, c2, c3, 1);
+            uint4 x = load_block(in + 16 * (m - 1), align);
+            const uint8_t* tail = in + 16 * m;
+            // both inputs are read before anything is written (in-place calls)
+            uint32_t yw[4] = {0, 0, 0, 0};
+            if (DIR == 0) block(x, a0, a1, a2, a3);  // CC
+            else block(x, c0, c1, c2, c3);           // PP
+            const uint32_t xw[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int k = 0; k < 16; k++) {
+                const uint32_t byte = (uint32_t)k < b ? (uint32_t)tail[k] : (xw[k >> 2] >> (8 * (k & 3))) & 0xffu;
+                yw[k >> 2] |= byte << (8 * (k & 3));
+            }
+            uint4 y = make_uint4(yw[0], yw[1], yw[2], yw[3]);
+            if (DIR == 0) block(y, c0, c1, c2, c3);  // C_{m-1}
+            else block(y, a0, a1, a2, a3);           // P_{m-1}
+            store_block(out + 16 * (m - 1), y, align);
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if ((uint32_t)k < b) out[16 * m + k] = (uint8_t)(xw[k >> 2] >> (8 * (k & 3)));
+        }
+    }
+}
+
 template <class P>
 using KernelFn = void (*)(P);
 
@@ -372,6 +490,15 @@ KernelFn<BulkParams> bulk_fn(int nr, int dir, bool tweak) {
         case 10: return pick_bulk<10>(dir, tweak);
         case 12: return pick_bulk<12>(dir, tweak);
         case 14: return pick_bulk<14>(dir, tweak);
+        default: return nullptr;
+    }
+}
+
+KernelFn<CtsParams> cts_fn(int nr, int dir) {
+    switch (nr) {
+        case 10: return dir ? xts_cts_kernel<10, 1> : xts_cts_kernel<10, 0>;
+        case 12: return dir ? xts_cts_kernel<12, 1> : xts_cts_kernel<12, 0>;
+        case 14: return dir ? xts_cts_kernel<14, 1> : xts_cts_kernel<14, 0>;
         default: return nullptr;
     }
 }
@@ -413,6 +540,11 @@ cudaError_t configure_kernels() {
         e = cudaFuncSetAttribute(cbc_enc_staged_fn(nr), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmemEncStaged);
         if (e != cudaSuccess) return e;
+        for (int dir = 0; dir < 2; dir++) {
+            e = cudaFuncSetAttribute(cts_fn(nr, dir), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(dir == 0 ? kSmemEnc : kSmemDec));
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -445,6 +577,16 @@ cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t
     if (!fn) return cudaErrorInvalidValue;
     int grid = grid_for(p.npages, num_sms);
     fn<<<grid, kBulkThreads, kSmemDec, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xts_cts(const CtsParams& p, int nr, int dir, int num_sms, cudaStream_t s) {
+    auto fn = cts_fn(nr, dir);
+    if (!fn) return cudaErrorInvalidValue;
+    const uint64_t warps = kBulkThreads / 32;
+    const uint64_t ctas = (p.units + warps - 1) / warps;
+    const int grid = (int)(ctas < (uint64_t)num_sms ? (ctas ? ctas : 1) : num_sms);
+    fn<<<grid, kBulkThreads, dir == 0 ? kSmemEnc : kSmemDec, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,20 @@ struct CbcParams {
     uint32_t rk[kMaxRoundKeyWords];
 };
 
+// XTS with ciphertext stealing: data units of du bytes, du >= 16 and not a
+// multiple of 16 (IEEE 1619-2007 5.3.2 / 5.4.2).  Unit u starts at byte u * du.
+struct CtsParams {
+    const uint8_t* src;
+    uint8_t* dst;
+    uint64_t units;
+    uint64_t du;
+    uint64_t first_sector;
+    uint32_t rk[kMaxRoundKeyWords];
+    uint32_t tk[kMaxRoundKeyWords];
+};
+
 cudaError_t launch_xts(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
+cudaError_t launch_xts_cts(const CtsParams& p, int nr, int dir, int num_sms, cudaStream_t s);
 cudaError_t launch_ecb(const BulkParams& p, int nr, int dir, int num_sms, cudaStream_t s);
 cudaError_t launch_cbc_dec(const CbcParams& p, int nr, int num_sms, cudaStream_t s);
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s);

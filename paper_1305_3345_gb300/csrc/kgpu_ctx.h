@@ -224,10 +224,12 @@ inline int get_key(kgpu_ctx* ctx, kgpu_key h, bool want_xts, HostKey* out) {
     return KGPU_OK;
 }
 
-inline int xts_args(kgpu_ctx* ctx, int dir, size_t len, size_t du, uint64_t first_sector) {
+// stealing: data units that are not a multiple of 16 bytes (at least 16) are
+// allowed and end with ciphertext stealing.
+inline int xts_args(kgpu_ctx* ctx, int dir, size_t len, size_t du, uint64_t first_sector, bool stealing = false) {
     if (!ctx) return KGPU_EINVAL;
     if (dir != KGPU_ENCRYPT && dir != KGPU_DECRYPT) return KGPU_EINVAL;
-    if (du == 0 || du % 16 || len % du) return KGPU_EINVAL;
+    if (du < 16 || (du % 16 && !stealing) || len % du) return KGPU_EINVAL;
     if (du / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
     uint64_t units = len / du;
     if (units && first_sector + (units - 1) < first_sector) return KGPU_EINVAL;  // 64-bit unit numbers

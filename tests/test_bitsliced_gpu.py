@@ -94,6 +94,7 @@ def test_bitsliced_argument_errors(ctx):
     f = L.kgpu_aes_xts_crypt_bitsliced
     assert f(h, kh, 1, p, p, 8192, 4096, 0, s) == -22          # decryption is table-only
     assert f(h, kh, 0, p, p, 8000, 4096, 0, s) == -22          # not whole units
+    assert f(h, kh, 0, p, p, 8002, 4001, 0, s) == -22          # partial blocks: table path only
     assert f(h, kh, 0, p, p + 16, 4096, 4096, 0, s) == -22     # partial overlap
     assert f(h, kh, 0, p, p, 1 << 40, 4096, 0, s) == -14       # past the allocation
     assert f(h, 999, 0, p, p, 4096, 4096, 0, s) == -2          # unknown key

@@ -62,6 +62,33 @@ def test_xts_vs_oracle(ctx, bits, du, units, first):
         assert np.array_equal(got, ref), (bits, du, units, dir)
 
 
+@pytest.mark.parametrize("bits", [128, 256])
+@pytest.mark.parametrize("du,units,first", [
+    (17, 301, 0),              # one full block + 1 byte: the stealing pair is the whole unit
+    (31, 100, 5),              # 15-byte tail
+    (100, 1000, 2**40 + 3),    # 4-byte aligned unit starts, more units than a CTA has warps
+    (527, 257, 2**63 - 300),   # odd unit starts (byte accesses)
+    (4100, 67, 11),            # 256 full blocks + 4 bytes
+    (4097, 33, 1),             # 256 full blocks + 1 byte, byte-aligned starts
+])
+def test_xts_ciphertext_stealing_vs_oracle(ctx, bits, du, units, first):
+    """Data units that are not a multiple of 16 bytes end with ciphertext
+    stealing (IEEE 1619 5.3.2 / 5.4.2), bit-exact with the oracle both ways
+    and in place."""
+    import torch
+    key = w.xts_key(8, bits)
+    data = w.seeded_bytes(8 + du, w.STREAM_DATA, du * units)
+    for dir in (ENC, DEC):
+        ref = oracle.xts(key, dir, data, du, first)
+        assert np.array_equal(run_xts(ctx, key, dir, data, du, first), ref), (bits, du, dir)
+    kh = ctx.setkey(key, True)
+    buf = to_dev(data)
+    ctx.xts_crypt(kh, ENC, buf, buf, du, first)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(buf), oracle.xts(key, ENC, data, du, first))
+    ctx.delkey(kh)
+
+
 def test_xts_tiny_and_single_unit(ctx):
     key = w.xts_key(4, 256)
     for du, units in ((16, 1), (4096, 1), (512, 1), (32, 3)):
@@ -111,7 +138,9 @@ def test_xts_argument_errors(ctx):
     s = torch.cuda.current_stream().cuda_stream
     assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p, 8192, 4096, 0, s) == 0
     assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p, 8000, 4096, 0, s) == -22     # not whole units
-    assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p, 8192, 4000, 0, s) == -22     # du % 16
+    assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p, 8002, 4001, 0, s) == 0       # du % 16: ciphertext stealing
+    assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p, 8192, 4001, 0, s) == -22     # not whole units
+    assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p, 80, 8, 0, s) == -22          # unit shorter than a block
     assert L.kgpu_aes_xts_crypt(h, kh, 2, p, p, 8192, 4096, 0, s) == -22     # bad direction
     assert L.kgpu_aes_xts_crypt(h, kh, 0, p + 8, p + 8, 4096, 4096, 0, s) == -22   # misaligned
     assert L.kgpu_aes_xts_crypt(h, kh, 0, p, p + 16, 4096, 4096, 0, s) == -22  # partial overlap
