@@ -756,9 +756,20 @@ def run_kgpu(args):
                       lambda: ctx.xts_crypt_bitsliced(kh, 0, src, dst, SECTOR, 0, stream)))
         specs.append(("aes128_xts_enc_4k_bitsliced",
                       lambda: ctx.xts_crypt_bitsliced(k128, 0, src, dst, SECTOR, 0, stream)))
+        # shared-memory lookups per 16-byte block of each table mode: Nr x 16,
+        # times (1 + 1/blocks per unit) for the XTS tweak; the bitsliced modes
+        # do no lookups (their bound is the ALU, see --variant bitsliced)
+        lookups = {"aes256_xts_dec_4k": 14 * 16 * 257 / 256, "aes256_xts_enc_512": 14 * 16 * 33 / 32,
+                   "aes128_xts_enc_4k": 10 * 16 * 257 / 256, "aes128_xts_dec_4k": 10 * 16 * 257 / 256,
+                   "aes128_cbc_dec_4k": 10 * 16, "aes128_cbc_enc_4k": 10 * 16, "aes128_ecb_enc": 10 * 16}
+        smem_bound_clk = props.multi_processor_count * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6
         for name, fn in specs:
             t = time_op(fn, 20, stream)
             extra[name] = {"GB/s": GIB / t / 1e9, "ms": t * 1e3}
+            if name in lookups:
+                bound = smem_bound_clk / (lookups[name] * 4) * 16 / 1e9
+                extra[name]["smem_bound_GB/s"] = bound
+                extra[name]["frac_of_smem_bound"] = GIB / t / 1e9 / bound
         line["extra"] = extra
         ctx.delkey(k128)
         ctx.delkey(ck)
