@@ -804,6 +804,29 @@ def run_kgpu(args):
         line["e2e"] = {"value": world * GIB / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": world * GIB,
                        "d2h_bytes_per_step": world * GIB, "steps": e2e_steps, "chunk_bytes": chunk,
                        "call": "kgpu_aes_xts_crypt_host (pinned host pages)"}
+        # the same step with the pages left in registered host memory: one
+        # batched request whose kernel reads and writes them over the link
+        ctx.host_register(hsrc)
+        ctx.host_register(hdst)
+        r = np.zeros(1, dtype=kg.request_dtype())
+        r["mode"], r["key"], r["src"], r["dst"] = kg.MODE_XTS, kh, hsrc.data_ptr(), hdst.data_ptr()
+        r["len"], r["unit_size"], r["flags"] = GIB, SECTOR, kg.REQ_SRC_HOST | kg.REQ_DST_HOST
+        ctx.poll(ctx.submit(r), -1)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.poll(ctx.submit(r), -1)
+        dz = (time.perf_counter() - t0) / e2e_steps
+        if dist:
+            t = torch.tensor([dz], device=f"cuda:{dev}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dz = float(t.item())
+        ctx.host_unregister(hsrc)
+        ctx.host_unregister(hdst)
+        line["e2e_zero_copy"] = {"value": world * GIB / dz / 1e9, "unit": "GB/s",
+                                 "link_bytes_per_step": {"host_to_device": world * GIB, "device_to_host": world * GIB},
+                                 "steps": e2e_steps, "call": "kgpu_submit + kgpu_poll, src/dst flagged host"}
         del hsrc, hdst
 
     if rank == 0 and not args.no_batched and (nbytes == GIB or args.batch_requests != 10000):
