@@ -291,6 +291,23 @@ int kgpu_submit(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream s
  */
 int kgpu_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *req_status);
 
+/*
+ * Wait for a ticket request by request: each request of the batch publishes
+ * its own completion as the warp that finishes its last tile writes a
+ * completion word in pinned host memory (after the request's output is in
+ * place), so small requests are done long before the batch ends.  Polls those
+ * words until every request is complete and writes, for each request i,
+ * done_ns[i] = the host's CLOCK_MONOTONIC time (ns) at which its completion
+ * was first seen (requests of zero length: the call's start).  Then behaves
+ * as kgpu_poll(..., -1, req_status).  done_ns: n entries, caller-owned.
+ * timeout_ns < 0: no limit; otherwise KGPU_ETIMEDOUT after that long with
+ * some requests still running (done_ns[i] = 0 for those).  While a call waits
+ * on a ticket, a kgpu_submit that would reuse its staging slot returns
+ * KGPU_EBUSY instead.  Errors: KGPU_EINVAL, KGPU_ENOENT (unknown or retired
+ * ticket), KGPU_EIO.
+ */
+int kgpu_poll_each(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *req_status, uint64_t *done_ns);
+
 /* Set / read the batch kernel's launch shape (validated: KGPU_EINVAL). */
 int kgpu_set_tuning(kgpu_ctx *ctx, const kgpu_tuning *t);
 int kgpu_get_tuning(kgpu_ctx *ctx, kgpu_tuning *t);

@@ -138,6 +138,7 @@ def lib() -> ctypes.CDLL:
                 "kgpu_replay_launches": ([vp, vp, vp, sz, u32, ctypes.c_int64, vp, ctypes.POINTER(u64)], i32),
                 "kgpu_submit_noalloc": ([vp, vp, sz, vp, vp], i32),
                 "kgpu_host_register": ([vp, vp, sz, u32], i32),
+                "kgpu_poll_each": ([vp, u64, ctypes.c_int64, vp, vp], i32),
                 "kgpu_aes_xts_crypt_bitsliced": ([vp, u32, i32, vp, vp, sz, sz, u64, vp], i32),
                 "kgpu_host_unregister": ([vp, vp], i32),
             }
@@ -311,6 +312,19 @@ def kgpu_poll(ctx, ticket: int, timeout_ns: int = -1, status=None) -> int:
     if rc == -110:
         return rc
     return _check(rc, "kgpu_poll")
+
+
+def kgpu_poll_each(ctx, ticket: int, n: int, timeout_ns: int = -1, status=None):
+    """Wait for every request of a batch; returns (rc, done_ns) with done_ns[i]
+    the CLOCK_MONOTONIC time (ns, as time.monotonic_ns()) at which request i
+    was seen complete."""
+    import numpy as np
+    done = np.zeros(n, dtype=np.uint64)
+    sp = status.ctypes.data if status is not None else None
+    rc = lib().kgpu_poll_each(ctx, ticket, timeout_ns, sp, done.ctypes.data)
+    if rc not in (0, -110):
+        _check(rc, "kgpu_poll_each")
+    return rc, done
 
 
 def kgpu_set_tuning(ctx, threads=0, tile_chunks=0, ctas=0) -> None:
@@ -507,6 +521,9 @@ class Context:
 
     def set_tuning(self, threads=0, tile_chunks=0, ctas=0):
         kgpu_set_tuning(self.handle, threads, tile_chunks, ctas)
+
+    def poll_each(self, ticket, n, timeout_ns=-1, status=None):
+        return kgpu_poll_each(self.handle, ticket, n, timeout_ns, status)
 
     def get_tuning(self) -> dict:
         return kgpu_get_tuning(self.handle)

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -61,7 +62,7 @@ int pack_batch(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, uint32_t tile_
     BatchHeader* h = reinterpret_cast<BatchHeader*>(buf);
     h->total_tiles = tiles;
     h->nreq = (uint32_t)n;
-    h->pad = 0;
+    h->tag = 0;
     return first;
 }
 
@@ -73,6 +74,8 @@ void free_slot(kgpu::BatchSlot& s) {
     if (s.d_buf) cudaFree(s.d_buf);
     if (s.h_status) cudaFreeHost(s.h_status);
     if (s.d_status) cudaFree(s.d_status);
+    if (s.d_fin) cudaFree(s.d_fin);
+    if (s.h_done) cudaFreeHost(s.h_done);
     if (s.d_counter) cudaFree(s.d_counter);
     if (s.d_scratch) cudaFree(s.d_scratch);
     if (s.done) cudaEventDestroy(s.done);
@@ -123,18 +126,28 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
         if (s.d_buf) cudaFree(s.d_buf);
         if (s.h_status) cudaFreeHost(s.h_status);
         if (s.d_status) cudaFree(s.d_status);
+        if (s.d_fin) cudaFree(s.d_fin);
+        if (s.h_done) cudaFreeHost(s.h_done);
         s.h_buf = nullptr;
         s.d_buf = nullptr;
         s.h_status = nullptr;
         s.d_status = nullptr;
+        s.d_fin = nullptr;
+        s.h_done = nullptr;
+        s.d_done = nullptr;
         s.cap = s.status_cap = 0;
         if (cudaHostAlloc(&s.h_buf, cap, cudaHostAllocDefault) != cudaSuccess ||
             cudaMalloc(&s.d_buf, cap) != cudaSuccess ||
             cudaHostAlloc(&s.h_status, scap * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
-            cudaMalloc(&s.d_status, scap * sizeof(int)) != cudaSuccess) {
+            cudaMalloc(&s.d_status, scap * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&s.d_fin, scap * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaHostAlloc(&s.h_done, scap * sizeof(unsigned long long), cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess ||
+            cudaHostGetDevicePointer(reinterpret_cast<void**>(&s.d_done), s.h_done, 0) != cudaSuccess) {
             cudaGetLastError();
             return KGPU_ENOMEM;
         }
+        std::memset(s.h_done, 0, scap * sizeof(unsigned long long));
         s.cap = cap;
         s.status_cap = scap;
         rebuild = true;
@@ -153,6 +166,8 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
     s.args.status = s.d_status;
     s.args.scratch = s.d_scratch;
     s.args.scratch_warps = s.scratch_warps;
+    s.args.fin = s.d_fin;
+    s.args.done = s.d_done;
 
     cudaGraph_t g = nullptr;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return KGPU_EIO;
@@ -169,6 +184,9 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
     mp.dst = s.d_status;
     mp.width = s.status_cap;
     ok = ok && cudaGraphAddMemsetNode(&s.n_status_clear, g, nullptr, 0, &mp) == cudaSuccess;
+    mp.dst = s.d_fin;
+    mp.width = 2 * s.status_cap;
+    ok = ok && cudaGraphAddMemsetNode(&s.n_fin_clear, g, nullptr, 0, &mp) == cudaSuccess;
     cudaKernelNodeParams kp{};
     void* kargs[] = {&s.args};
     kp.func = const_cast<void*>(batch_kernel_fn((int)t.threads));
@@ -176,8 +194,8 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
     kp.blockDim = dim3(t.threads);
     kp.sharedMemBytes = (unsigned)unified_smem_bytes((int)t.threads);
     kp.kernelParams = kargs;
-    cudaGraphNode_t deps[3] = {s.n_copy, n_ctr, s.n_status_clear};
-    ok = ok && kp.func && cudaGraphAddKernelNode(&s.n_kernel, g, deps, 3, &kp) == cudaSuccess;
+    cudaGraphNode_t deps[4] = {s.n_copy, n_ctr, s.n_status_clear, s.n_fin_clear};
+    ok = ok && kp.func && cudaGraphAddKernelNode(&s.n_kernel, g, deps, 4, &kp) == cudaSuccess;
     ok = ok && cudaGraphAddMemcpyNode1D(&s.n_status_out, g, &s.n_kernel, 1, s.h_status, s.d_status,
                                         s.status_cap * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && cudaGraphInstantiate(&s.exec, g, 0) == cudaSuccess;
@@ -204,6 +222,9 @@ int launch_slot(kgpu::BatchSlot& s, size_t n, cudaStream_t stream) {
     mp.width = n;
     mp.height = 1;
     ok = ok && cudaGraphExecMemsetNodeSetParams(s.exec, s.n_status_clear, &mp) == cudaSuccess;
+    mp.dst = s.d_fin;
+    mp.width = 2 * n;
+    ok = ok && cudaGraphExecMemsetNodeSetParams(s.exec, s.n_fin_clear, &mp) == cudaSuccess;
     ok = ok && cudaGraphExecMemcpyNodeSetParams1D(s.exec, s.n_status_out, s.h_status, s.d_status, n * sizeof(int),
                                                   cudaMemcpyDeviceToHost) == cudaSuccess;
     ok = ok && cudaGraphLaunch(s.exec, stream) == cudaSuccess;
@@ -267,6 +288,11 @@ int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream s
     if (t.threads > 512 && needs_staging(reqs, n)) t.threads = 512;
     const uint64_t ticket = ++ctx->next_ticket;
     kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
+    // a batch someone waits on with kgpu_poll_each keeps its slot
+    if (s.pollers > 0) {
+        --ctx->next_ticket;
+        return KGPU_EBUSY;
+    }
     // rotate: the slot's previous batch must have finished before its
     // staging buffers are refilled
     if (s.issued && cudaEventSynchronize(s.done) != cudaSuccess) {
@@ -280,6 +306,8 @@ int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream s
     if (rc) return rc;
     s.nreq = (uint32_t)n;
     s.gen = ticket;
+    s.tag = (uint32_t)(ticket % 0xFFFFFFFFull) + 1u;  // never 0, the value of a fresh word
+    reinterpret_cast<BatchHeader*>(s.h_buf)->tag = s.tag;
     if (n) {
         if ((rc = launch_slot(s, n, (cudaStream_t)stream))) return rc;
     } else if (cudaEventRecord(s.done, (cudaStream_t)stream) != cudaSuccess) {
@@ -289,6 +317,59 @@ int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream s
     s.issued = true;
     *out = ticket;
     return KGPU_OK;
+}
+
+int kgpu_poll_each(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* req_status, uint64_t* done_ns) {
+    if (!ctx || !done_ns) return KGPU_EINVAL;
+    const unsigned long long* words;
+    uint32_t n, tag;
+    std::vector<uint8_t> empty;  // requests with no tiles (len 0) complete at once
+    {
+        std::lock_guard<std::mutex> lk(ctx->batch_mu);
+        kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
+        if (ticket == 0 || s.gen != ticket || !s.issued) return KGPU_ENOENT;
+        words = s.h_done;
+        n = s.nreq;
+        tag = s.tag;
+        s.pollers++;
+        const ReqDesc* descs = reinterpret_cast<const ReqDesc*>(s.h_buf + batch_desc_offset());
+        empty.resize(n);
+        for (uint32_t i = 0; i < n; i++) empty[i] = descs[i].nblocks == 0;
+    }
+    auto now = []() {
+        return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                   std::chrono::steady_clock::now().time_since_epoch())
+            .count();
+    };
+    const uint64_t t0 = now();
+    const uint64_t deadline = timeout_ns < 0 ? UINT64_MAX : t0 + (uint64_t)timeout_ns;
+    std::vector<uint32_t> pending;
+    pending.reserve(n);
+    for (uint32_t i = 0; i < n; i++) {
+        done_ns[i] = 0;
+        if (empty[i]) done_ns[i] = t0;
+        else pending.push_back(i);
+    }
+    int rc = KGPU_OK;
+    while (!pending.empty()) {
+        const uint64_t t = now();
+        size_t keep = 0;
+        for (uint32_t i : pending) {
+            const unsigned long long v = __atomic_load_n(&words[i], __ATOMIC_ACQUIRE);
+            if ((uint32_t)(v >> 32) == tag) done_ns[i] = t;
+            else pending[keep++] = i;
+        }
+        pending.resize(keep);
+        if (!pending.empty() && t >= deadline) {
+            rc = KGPU_ETIMEDOUT;
+            break;
+        }
+    }
+    // every request is complete; the status copy ends the batch's graph
+    if (!rc) rc = kgpu_poll(ctx, ticket, -1, req_status);
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    ctx->slots[ticket % kBatchSlots].pollers--;
+    return rc;
 }
 
 int kgpu_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* req_status) {

@@ -28,13 +28,19 @@ struct BatchSlot {
     int* d_status = nullptr;
     int* h_status = nullptr;     // pinned
     size_t status_cap = 0;       // entries
+    unsigned long long* d_fin = nullptr;   // per request: tiles finished
+    unsigned long long* h_done = nullptr;  // pinned, mapped: per-request completion words
+    unsigned long long* d_done = nullptr;  // the device's view of h_done
+    uint32_t tag = 0;                      // completion tag of the slot's current batch
+    int pollers = 0;                       // kgpu_poll_each calls holding the slot
     unsigned long long* d_counter = nullptr;
     uint4* d_scratch = nullptr;  // per-warp staging for CBC encryption of host pages
     uint32_t scratch_warps = 0;
     uint32_t nreq = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t n_copy = nullptr, n_status_clear = nullptr, n_kernel = nullptr, n_status_out = nullptr;
+    cudaGraphNode_t n_copy = nullptr, n_status_clear = nullptr, n_fin_clear = nullptr, n_kernel = nullptr,
+                    n_status_out = nullptr;
     int graph_threads = 0, graph_grid = 0;
     BatchArgs args{};
 };

@@ -78,7 +78,7 @@ __host__ __device__ inline uint64_t request_units(const ReqDesc& d) {
 struct BatchHeader {
     uint64_t total_tiles;
     uint32_t nreq;
-    uint32_t pad;
+    uint32_t tag;  // low 32 bits of the batch's ticket, in its completion words
 };
 
 // Byte layout of a batch on the device: header, descriptors, tile prefix, run order.
@@ -105,6 +105,8 @@ struct BatchArgs {
     unsigned long long* next_tile;  // work counter (zero before launch)
     int* status;                    // per request: 0, or a negative KGPU_E* set by the kernel
     uint4* scratch;                 // kStageWarpBytes per warp, or null
+    unsigned long long* fin;        // per request: tiles finished (zero before launch), or null
+    unsigned long long* done;       // per request, host-mapped: tag << 32 | status once complete
 };
 
 // ---------------------------------------------------------------------------

@@ -118,7 +118,7 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
     BatchHeader* h = reinterpret_cast<BatchHeader*>(g_pack);
     h->total_tiles = tiles;
     h->nreq = (uint32_t)n;
-    h->pad = 0;
+    h->tag = 0;
 
     cudaStream_t s = (cudaStream_t)stream;
     BatchArgs a{};

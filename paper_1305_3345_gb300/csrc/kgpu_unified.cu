@@ -338,6 +338,40 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
     return 0;
 }
 
+// Memory-order helpers (PTX scopes: gpu = this device, sys = with the host).
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_gpu32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(128) char smem[];
@@ -376,6 +410,20 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
         const ReqDesc d = reqs[i];
         const int st = run_tile(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
         if (st && lane == 0) a.status[i] = st;
+        if (a.fin) {
+            // per-request completion: the warp that finishes a request's last
+            // tile publishes (tag << 32 | status) to the host-mapped word,
+            // after an acq_rel count that orders every warp's tile writes
+            // before it (the same protocol as the serving ring)
+            __syncwarp();
+            unsigned long long f = 0;
+            if (lane == 0) f = atom_add_acq_rel_gpu(&a.fin[i], 1ull) + 1;
+            f = __shfl_sync(0xffffffffu, f, 0);
+            if (lane == 0 && f == tile_start[k + 1] - tile_start[k]) {
+                const unsigned int code = (unsigned int)*reinterpret_cast<volatile int*>(&a.status[i]);
+                st_release_sys(&a.done[i], (unsigned long long)hdr->tag << 32 | code);
+            }
+        }
         next = __shfl_sync(0xffffffffu, next, 0);
     }
 }
@@ -402,41 +450,6 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
 // never published are handed back by serve_reset_kernel before a relaunch.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long* p) {
-    return *reinterpret_cast<const volatile unsigned long long*>(p);
-}
-__device__ __forceinline__ unsigned int ld_vol32(const unsigned int* p) {
-    return *reinterpret_cast<const volatile unsigned int*>(p);
-}
-__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long atom_add_acq_rel_gpu(unsigned long long* p, unsigned long long v) {
-    unsigned long long old;
-    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void st_release_gpu32(unsigned int* p, unsigned int v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
     const uint32_t lane = lane_id();

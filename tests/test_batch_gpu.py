@@ -248,3 +248,47 @@ def test_batched_workload_full_shape_sampled(ctx):
         ctx.delkey(h)
     del src, dst, ivs
     torch.cuda.empty_cache()
+
+
+def test_poll_each_reports_every_request(ctx):
+    """Per-request completion words: every request of a batch is seen complete,
+    no earlier than the submission and no later than the batch, with the same
+    bytes as a batch waited on as a whole; a zero-length request is complete at
+    once."""
+    import time
+    import torch
+    import paper_1305_3345_gb300 as kg
+    mix = w.request_mix(61, 120, 4096, 2 << 20, 8)
+    keys = w.mix_key_material(61, mix)
+    hx = [ctx.setkey(k[: 2 * b // 8], True) for k, b in zip(keys, mix.key_bits)]
+    hs = [ctx.setkey(k[: b // 8], False) for k, b in zip(keys, mix.key_bits)]
+    src = torch.from_numpy(w.seeded_bytes(61, w.STREAM_DATA, mix.total_bytes)).cuda()
+    outs = [torch.zeros_like(src), torch.zeros_like(src)]
+    npages = mix.sizes // 4096
+    ivs = torch.from_numpy(w.page_ivs(61, int(npages.sum())).reshape(-1).copy()).cuda()
+    iv_off = np.concatenate([[0], np.cumsum(npages)[:-1]])
+    arrays = []
+    for out in outs:
+        r = np.zeros(len(mix.sizes), dtype=kg.request_dtype())
+        cbc = (mix.modes == w.MODE_CBC_DEC) | (mix.modes == w.MODE_CBC_ENC)
+        r["mode"], r["dir"] = mix.modes, np.where(cbc, 0, mix.dirs)
+        r["key"] = np.where(mix.modes == w.MODE_XTS, np.array(hx)[mix.keys], np.array(hs)[mix.keys])
+        r["src"], r["dst"] = src.data_ptr() + mix.offsets, out.data_ptr() + mix.offsets
+        r["len"], r["unit_size"], r["sector"] = mix.sizes, 4096, mix.offsets // 4096
+        r["ivs"] = np.where(cbc, ivs.data_ptr() + 16 * iv_off, 0)
+        r["len"][5] = 0                      # one empty request
+        arrays.append(r)
+    torch.cuda.synchronize()
+    assert ctx.poll(ctx.submit(arrays[0]), -1) == 0
+    st = np.full(len(mix.sizes), 9, np.int32)
+    t0 = time.monotonic_ns()
+    t = ctx.submit(arrays[1])
+    rc, done = ctx.poll_each(t, len(mix.sizes), status=st)
+    t1 = time.monotonic_ns()
+    assert rc == 0 and not st.any()
+    assert (done >= t0).all() and (done <= t1).all()
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1])
+    assert ctx.poll(t, 0) == 0               # the ticket stays valid afterwards
+    for h in hx + hs:
+        ctx.delkey(h)
