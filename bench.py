@@ -405,6 +405,28 @@ def run_serving(ctx, kg, dev, seconds, host=False):
                                         ((w.MODE_XTS, "xts"), (w.MODE_CBC_DEC, "cbc_dec"),
                                          (w.MODE_CBC_ENC, "cbc_enc")) if (mix.modes == m).any()}},
         })
+    capacity = None
+    if not host:
+        # past saturation, ring only: 3M requests/s (~560 GB/s offered) for
+        # half the trace length shows what the ring sustains (one launch per
+        # request saturates near 27 GB/s and would need tens of seconds here)
+        rate = 3_000_000
+        n = int(rate * seconds / 2)
+        mix = w.request_mix(5 + rate, n, 4096, 1 << 20, nkeys)
+        mix.key_bits = key_mix.key_bits
+        reqs = build_requests(kg, mix, hx, hs, src, pool_in, dst, pool_out, ivs, 5 + rate)
+        arr = (w.poisson_arrivals(5 + rate, n, float(rate)) * 1e9).astype(np.uint64)
+        ctx.serve_start(admit_bytes=8 * GIB)
+        try:
+            with ClockSampler(dev) as clk_cap:
+                rc, lat, wall = ctx.replay_serve(reqs, arr, timeout_ns=120_000_000_000)
+            stats = ctx.serve_stats()
+        finally:
+            ctx.serve_stop(30_000_000_000)
+        total = int(mix.sizes.sum())
+        capacity = {"rate_req_s": rate, "requests": n, "offered_GB/s": total / (float(arr[-1]) / 1e9) / 1e9,
+                    "ring": {"GB/s": total / (wall / 1e9) / 1e9, "rc": rc, "latency": pct(lat),
+                             "busy_refusals": stats["busy_refusals"], "clocks": clk_cap.summary()}}
     for h in list(hx) + list(hs):
         ctx.delkey(int(h))
     if host:
@@ -417,7 +439,7 @@ def run_serving(ctx, kg, dev, seconds, host=False):
     return {"workload": "Poisson arrivals, sizes 4 KiB..1 MiB log-uniform, 1024 keys (AES-128/256), "
                         "50% XTS / 25% CBC-dec / 25% CBC-enc, admission cap 8 GiB, "
                         f"{seconds:g} s per rate; {where}",
-            "rates": res}
+            "rates": res, "ring_capacity": capacity}
 
 
 def run_host_stream(ctx, kg, kh, dev):

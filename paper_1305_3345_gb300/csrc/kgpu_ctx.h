@@ -300,6 +300,20 @@ int resolve_buffer(kgpu_ctx* ctx, Cache& rc, const void* p, size_t len, bool hos
 
 constexpr uint32_t kReqFlagsAll = KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST | KGPU_REQ_IVS_HOST;
 
+// Work units per tile for a tile of tile_chunks 512-byte chunks: XTS/ECB
+// count 32-block chunks; CBC decryption whole pages of about the same bytes;
+// CBC encryption 32 pages, one chain per lane.
+inline void set_tile_units(ReqDesc& d, uint32_t tile_chunks) {
+    if (d.mode == KGPU_MODE_CBC_ENC) {
+        d.tile_units = 32;
+    } else if (d.mode == KGPU_MODE_CBC_DEC) {
+        uint64_t ppt = (uint64_t)tile_chunks * 32 / d.unit_blocks;
+        d.tile_units = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ppt, 1u << 30));
+    } else {
+        d.tile_units = std::max<uint32_t>(1, tile_chunks);
+    }
+}
+
 // Validate one request and write its device descriptor (tile size in 512-B
 // chunks for XTS/ECB; CBC tiles derive from it).  Cache: anything with
 // int check(const kgpu_ctx*, const void*, size_t) -- RangeCache, or a
@@ -352,14 +366,7 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
     d->mode = q.mode;
     d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : q.dir;
     d->host = ((q.flags & KGPU_REQ_SRC_HOST) ? kDescSrcHost : 0u) | ((q.flags & KGPU_REQ_DST_HOST) ? kDescDstHost : 0u);
-    if (q.mode == KGPU_MODE_CBC_ENC) {
-        d->tile_units = 32;  // one chain per lane
-    } else if (q.mode == KGPU_MODE_CBC_DEC) {
-        uint64_t ppt = (uint64_t)tile_chunks * 32 / d->unit_blocks;
-        d->tile_units = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(ppt, 1u << 30));
-    } else {
-        d->tile_units = std::max<uint32_t>(1, tile_chunks);
-    }
+    set_tile_units(*d, tile_chunks);
     return KGPU_OK;
 }
 
