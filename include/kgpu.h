@@ -371,6 +371,19 @@ int kgpu_serve_start(kgpu_ctx *ctx, const kgpu_serve_config *cfg);
 int kgpu_serve_submit(kgpu_ctx *ctx, const kgpu_request *req, kgpu_ticket *ticket);
 
 /*
+ * Publish several requests at once (a writeback of many pages, say): all n
+ * are validated first (any malformed one: its code is returned and nothing is
+ * published); then they are placed on the ring in order, as long as slots and
+ * the byte cap allow, and made visible to the device with one update of the
+ * ring head.  *accepted receives how many were published; tickets[0..accepted)
+ * their tickets.  Returns KGPU_OK when all were, KGPU_EBUSY when the ring or
+ * the cap stopped the rest (retry those), KGPU_EINVAL when serving is not
+ * started.
+ */
+int kgpu_serve_submit_many(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_ticket *tickets,
+                           size_t *accepted);
+
+/*
  * Wait for a served request.  timeout_ns: 0 = check once, < 0 = wait until
  * done, > 0 = wait at most that long.  KGPU_OK when complete (*status, if not
  * NULL: 0 or the request's KGPU_E* code; stamps, if not NULL: the device's

@@ -139,6 +139,7 @@ def lib() -> ctypes.CDLL:
                 "kgpu_submit_noalloc": ([vp, vp, sz, vp, vp], i32),
                 "kgpu_host_register": ([vp, vp, sz, u32], i32),
                 "kgpu_poll_each": ([vp, u64, ctypes.c_int64, vp, vp], i32),
+                "kgpu_serve_submit_many": ([vp, vp, sz, vp, ctypes.POINTER(sz)], i32),
                 "kgpu_aes_xts_crypt_bitsliced": ([vp, u32, i32, vp, vp, sz, sz, u64, vp], i32),
                 "kgpu_host_unregister": ([vp, vp], i32),
             }
@@ -415,6 +416,21 @@ def kgpu_serve_submit(ctx, req) -> int:
     return t.value
 
 
+def kgpu_serve_submit_many(ctx, reqs):
+    """Publish a batch of requests onto the ring in one burst; returns (rc,
+    tickets of the accepted prefix).  rc is 0, or KGPU_EBUSY (-16) when the
+    ring stopped the rest; other errors raise."""
+    import numpy as np
+    ptr, n, keep = _req_array(reqs)
+    tickets = np.zeros(n, dtype=np.uint64)
+    acc = ctypes.c_size_t()
+    rc = lib().kgpu_serve_submit_many(ctx, ptr, n, tickets.ctypes.data, ctypes.byref(acc))
+    del keep
+    if rc not in (0, -16):
+        _check(rc, "kgpu_serve_submit_many")
+    return rc, tickets[: acc.value]
+
+
 def kgpu_serve_poll(ctx, ticket: int, timeout_ns: int = -1):
     """(rc, status, (t_first_tile, t_done)) -- rc 0 when complete, -110 while pending."""
     st = ctypes.c_int()
@@ -542,6 +558,9 @@ class Context:
 
     def serve_start(self, **kw):
         kgpu_serve_start(self.handle, **kw)
+
+    def serve_submit_many(self, reqs):
+        return kgpu_serve_submit_many(self.handle, reqs)
 
     def serve_submit(self, req) -> int:
         return kgpu_serve_submit(self.handle, req)

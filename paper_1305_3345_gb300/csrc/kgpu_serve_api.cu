@@ -181,7 +181,29 @@ void reap(ServeState& st) {
 }
 
 // Publish a validated descriptor.  Caller holds serve_mu.
-int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) {
+// Tile size of requests staged while the ring is backed up (512-byte chunks).
+constexpr uint32_t kBacklogTileChunks = 64;  // 32 KiB
+
+// Write one request into the next ring slot, without making it visible to
+// the device yet (commit does that).  Caller holds serve_mu.
+//
+// Under backlog -- the request published a quarter of the ring ago is still
+// running -- a new request waits behind the queue whatever its tile size, so
+// it gets 32-KiB tiles: per tile the workers claim a position, reload a key
+// schedule and (for XTS) run a 32-unit tweak batch, and on 4-KiB tiles those
+// costs cap the ring's throughput.  A ring that keeps up keeps the configured
+// (default 4-KiB) tiles and their lower latency.  The check is one load of a
+// completion word, whatever the number of requests in flight.
+bool backlogged(const ServeState& st) {
+    const uint64_t q = st.nslots / 4;
+    if (st.next_seq < q) return false;
+    const uint64_t seq = st.next_seq - q;
+    return load_acquire(&st.done_seq[seq & (st.nslots - 1)]) < seq + 1;
+}
+
+int stage(ServeState& st, const ReqDesc& dreq, uint64_t* seq_out) {
+    ReqDesc d = dreq;
+    if (backlogged(st)) set_tile_units(d, std::max<uint32_t>(st.tile_chunks, kBacklogTileChunks));
     const uint64_t len = d.nblocks * 16;
     const uint64_t units = request_units(d);
     const uint64_t nt = (units + d.tile_units - 1) / d.tile_units;
@@ -205,7 +227,6 @@ int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) 
     st.status[s] = 0;
     st.t_start[s] = 0;
     st.t_done[s] = 0;
-    store_release(&st.hdr->head, (unsigned long long)(seq + 1));
     st.slot_busy[s] = 1;
     st.slot_seq[s] = seq;
     st.slot_len[s] = len;
@@ -214,12 +235,25 @@ int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) 
     st.next_seq++;
     st.submitted++;
     *seq_out = seq;
+    return KGPU_OK;
+}
+
+// Publish every staged request with one release store of the ring head (the
+// device's dispatcher polls that word over the host link, so one store per
+// burst instead of one per request), then make sure a kernel is running.
+int commit(kgpu_ctx* ctx, ServeState& st) {
+    store_release(&st.hdr->head, (unsigned long long)st.next_seq);
     const uint64_t t = now_ns();
     if (!st.running || t - st.last_alive_check > 20000) {
         st.last_alive_check = t;
         return ensure_running(ctx, st);
     }
     return KGPU_OK;
+}
+
+int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) {
+    int r = stage(st, d, seq_out);
+    return r ? r : commit(ctx, st);
 }
 
 }  // namespace
@@ -284,6 +318,36 @@ int kgpu_serve_submit(kgpu_ctx* ctx, const kgpu_request* req, kgpu_ticket* ticke
     uint64_t seq = 0;
     r = publish(ctx, st, d, &seq);
     if (r == KGPU_OK || r == KGPU_EIO) *ticket = seq + 1;
+    return r;
+}
+
+int kgpu_serve_submit_many(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_ticket* tickets,
+                           size_t* accepted) {
+    if (!ctx || !accepted || (n && (!reqs || !tickets))) return KGPU_EINVAL;
+    *accepted = 0;
+    if (n == 0) return KGPU_OK;
+    std::vector<ReqDesc> descs(n);
+    RangeCache rc;
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    if (!st.started) return KGPU_EINVAL;
+    for (size_t i = 0; i < n; i++) {  // all or nothing on validation
+        if (reqs[i].len == 0) return KGPU_EINVAL;
+        int r = make_desc(ctx, reqs[i], rc, st.tile_chunks, &descs[i]);
+        if (r) return r;
+    }
+    size_t k = 0;
+    int r = KGPU_OK;
+    for (; k < n; k++) {
+        uint64_t seq = 0;
+        if ((r = stage(st, descs[k], &seq))) break;
+        tickets[k] = seq + 1;
+    }
+    *accepted = k;
+    if (k) {
+        const int c = commit(ctx, st);
+        if (c) return c;
+    }
     return r;
 }
 
@@ -448,37 +512,42 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
         }
     });
 
+    // Producer: at each step, every request whose arrival time has passed is
+    // staged and the burst is committed with one head update, as a caller
+    // with several pages ready at once would do through kgpu_serve_submit_many.
     int rc = KGPU_OK;
-    for (size_t i = 0; i < n && !rc; i++) {
+    for (size_t i = 0; i < n && !rc;) {
         const uint64_t target = t0 + arrival_ns[i];
         for (;;) {
             const uint64_t t = now_ns();
             if (t >= target) break;
             if (target - t > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
-        for (;;) {
-            uint64_t seq = 0;
-            int r;
-            {
-                std::lock_guard<std::mutex> lk(ctx->serve_mu);
-                r = publish(ctx, st, descs[i], &seq);
+        size_t j = i;
+        int r = KGPU_OK;
+        {
+            std::lock_guard<std::mutex> lk(ctx->serve_mu);
+            const uint64_t t = now_ns();
+            for (; j < n && j - i < 256 && t0 + arrival_ns[j] <= t; j++) {
+                uint64_t seq = 0;
+                r = stage(st, descs[j], &seq);
+                if (r) break;
+                if (detail) detail[3 * j] = t - (t0 + arrival_ns[j]);
+                seq_of[j].store(seq, std::memory_order_release);
             }
-            if (r == KGPU_OK) {
-                if (detail) detail[3 * i] = now_ns() - target;
-                seq_of[i].store(seq, std::memory_order_release);
-                produced.store(i + 1, std::memory_order_release);
-                break;
+            if (j > i) {
+                const int c = commit(ctx, st);
+                if (c) r = c;
             }
-            if (r != KGPU_EBUSY) {
-                rc = r;
-                break;
-            }
-            if (now_ns() > deadline) {
-                rc = KGPU_ETIMEDOUT;
-                break;
-            }
-            cpu_relax();
         }
+        if (j > i) produced.store(j, std::memory_order_release);
+        if (r && r != KGPU_EBUSY) {
+            rc = r;
+        } else if (j == i) {  // refused: the ring or the byte cap is full
+            if (now_ns() > deadline) rc = KGPU_ETIMEDOUT;
+            else cpu_relax();
+        }
+        i = j;
         if (error.load()) rc = error.load();
     }
     if (rc) abort.store(true);

@@ -278,3 +278,30 @@ def test_serve_rejects_bad_requests(ctx):
     finally:
         assert ctx.serve_stop(5_000_000_000) == 0
     t.close()
+
+
+def test_serve_submit_many_bursts(ctx):
+    """A burst published with one head update: every result equals the oracle;
+    with a small ring the accepted prefix runs and the rest is retried."""
+    t = Traffic(ctx, seed=79, n=60, lo=4096, hi=128 << 10, nkeys=8)
+    ctx.serve_start(ring_slots=16)
+    try:
+        arr = t.array()
+        tickets = []
+        k = 0
+        while k < len(arr):
+            rc, tk = ctx.serve_submit_many(arr[k:])
+            assert rc in (0, -16)
+            tickets += list(tk)
+            k += len(tk)
+            if rc == -16 and len(tk) == 0:
+                time.sleep(0.0005)
+        assert len(tickets) == len(arr)
+        for tk in tickets:
+            rc, st, _ = ctx.serve_poll(int(tk), 10_000_000_000)
+            assert rc == 0 and st == 0
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    for i in range(len(t.reqs)):
+        assert np.array_equal(t.got(i), t.expected(i)), (i, int(t.modes[i]))
+    t.close()
