@@ -337,7 +337,10 @@ int kgpu_autotune(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream
 
 typedef struct kgpu_serve_config {
     uint32_t ring_slots;       /* ring capacity, power of two (0: the context's ring_slots) */
-    uint32_t tile_chunks;      /* XTS/ECB tile in 512-byte chunks (0: 8, i.e. 4 KiB) */
+    uint32_t tile_chunks;      /* XTS/ECB tile in 512-byte chunks (0: 8, i.e. 4 KiB); requests
+                                  published while the ring is backed up (the request
+                                  published a quarter of the ring earlier still running)
+                                  use at least 64 (32 KiB) for throughput */
     uint64_t admit_bytes;      /* cap on bytes in flight (0: the context's admit_bytes) */
     uint64_t idle_timeout_ns;  /* the kernel exits after this long with nothing to do
                                   (0: the context's idle_timeout_ns); it is relaunched
