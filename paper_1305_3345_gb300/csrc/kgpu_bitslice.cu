@@ -6,6 +6,14 @@
 // AddRoundKey are XORs of planes.  No table lookups: the work runs on the ALU
 // pipe (LOP3), not the shared-memory path the table kernels are bound by.
 //
+// Occupancy: the state alone is 128 registers; left to itself the compiler
+// uses 254 and the SM holds 8 warps, too few to hide the ALU's fixed latencies
+// and the instruction fetch over a ~2,500-instruction round.  At 384 threads
+// per CTA it fits 168 registers and spills a few hundred bytes to local
+// memory -- traffic on the LSU path, which this kernel otherwise leaves idle
+// -- and 12 warps run 18-20% faster (measured: 256 -> 167 GB/s,
+// 384 -> 197-201, 512 with 128 registers -> 130).
+//
 // Data layout: a warp owns a span of 1024 consecutive blocks; lane l takes
 // blocks l, l+32, ..., l+992, so each of its 32 loads and stores is one
 // coalesced 512-byte warp access.  A 32x32 bit transpose per state word turns

@@ -176,7 +176,7 @@ constexpr int kMboxStride = 16;  // words between two CTAs' mailboxes (128 B)
 inline uint64_t serve_max_tiles(uint64_t tile_ring) { return tile_ring / 2; }
 
 // Bitsliced kernels (kgpu_bitslice.cu): 32 blocks per thread as 128 bit-planes.
-constexpr int kBsThreads = 256;
+constexpr int kBsThreads = 384;  // 168 registers: 12 warps per SM (see the kernel's comment)
 struct BsParams {
     const uint4* src;
     uint4* dst;
