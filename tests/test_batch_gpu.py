@@ -292,3 +292,68 @@ def test_poll_each_reports_every_request(ctx):
     assert ctx.poll(t, 0) == 0               # the ticket stays valid afterwards
     for h in hx + hs:
         ctx.delkey(h)
+
+
+def test_concurrent_submitters_share_the_slots(ctx):
+    """Four host threads submit and wait on batches through one context at the
+    same time (they share the four rotating staging slots, and some wait
+    request by request); every output equals the oracle's."""
+    import threading
+    import torch
+    import paper_1305_3345_gb300 as kg
+    key = w.xts_key(71, 256)
+    kh = ctx.setkey(key, True)
+    nthreads, rounds, per = 4, 6, 16
+    data = w.seeded_bytes(71, w.STREAM_DATA, nthreads * per * 8192)
+    src = torch.from_numpy(data.copy()).cuda()
+    outs = [torch.zeros_like(src) for _ in range(nthreads)]
+    torch.cuda.synchronize()
+    errors = []
+
+    def worker(t):
+        try:
+            for k in range(rounds):
+                r = np.zeros(per, dtype=kg.request_dtype())
+                base = t * per * 8192
+                r["mode"], r["key"], r["len"], r["unit_size"] = w.MODE_XTS, kh, 8192, 4096
+                r["src"] = src.data_ptr() + base + 8192 * np.arange(per)
+                r["dst"] = outs[t].data_ptr() + base + 8192 * np.arange(per)
+                r["sector"] = (base + 8192 * np.arange(per)) // 4096
+                r["dir"] = k % 2                   # encrypt, then decrypt back, ...
+                if k % 2 == 0:
+                    r["src"] = src.data_ptr() + base + 8192 * np.arange(per)
+                else:
+                    r["src"] = r["dst"]            # in place on the previous result
+                while True:
+                    try:
+                        tk = ctx.submit(r)
+                        break
+                    except kg.KgpuError as e:      # the slot is held by a poll_each
+                        if e.code != "EBUSY":
+                            raise
+                if t % 2:
+                    rc, _ = ctx.poll_each(tk, per)
+                else:
+                    rc = ctx.poll(tk, -1)
+                assert rc == 0
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    ths = [threading.Thread(target=worker, args=(t,)) for t in range(nthreads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join(120)
+    assert not errors, errors
+    torch.cuda.synchronize()
+    # an even number of rounds: encrypt/decrypt pairs leave every output equal to the input
+    for t in range(nthreads):
+        a, b = t * per * 8192, (t + 1) * per * 8192
+        assert torch.equal(outs[t][a:b], src[a:b]), t
+    # and one encryption equals the oracle
+    r = np.zeros(1, dtype=kg.request_dtype())
+    r["mode"], r["key"], r["len"], r["unit_size"] = w.MODE_XTS, kh, 8192, 4096
+    r["src"], r["dst"], r["sector"] = src.data_ptr(), outs[0].data_ptr(), 0
+    assert ctx.poll(ctx.submit(r), -1) == 0
+    assert np.array_equal(outs[0][:8192].cpu().numpy(), oracle.xts(key, 0, data[:8192], 4096, 0))
+    ctx.delkey(kh)
