@@ -69,11 +69,34 @@ __device__ __forceinline__ void transpose32(uint32_t* a) {
     }
 }
 
+// One S-box circuit, called 16 times a round rather than inlined 16 times: the
+// round body shrinks by ~1,500 instructions, which eases the instruction fetch
+// stalls that top this kernel's profile (measured +4%, for 16 argument moves
+// per call).
+struct Byte8 {
+    uint32_t x0, x1, x2, x3, x4, x5, x6, x7;
+};
+
+__device__ __noinline__ Byte8 sbox_call(Byte8 b) {
+    sbox_circuit(b.x0, b.x1, b.x2, b.x3, b.x4, b.x5, b.x6, b.x7);
+    return b;
+}
+
 __device__ __forceinline__ void sub_bytes(uint32_t (&S)[128]) {
 #pragma unroll
-    for (int p = 0; p < 16; p++)
-        sbox_circuit(S[8 * p + 0], S[8 * p + 1], S[8 * p + 2], S[8 * p + 3], S[8 * p + 4], S[8 * p + 5],
-                     S[8 * p + 6], S[8 * p + 7]);
+    for (int p = 0; p < 16; p++) {
+        Byte8 b{S[8 * p + 0], S[8 * p + 1], S[8 * p + 2], S[8 * p + 3],
+                S[8 * p + 4], S[8 * p + 5], S[8 * p + 6], S[8 * p + 7]};
+        b = sbox_call(b);
+        S[8 * p + 0] = b.x0;
+        S[8 * p + 1] = b.x1;
+        S[8 * p + 2] = b.x2;
+        S[8 * p + 3] = b.x3;
+        S[8 * p + 4] = b.x4;
+        S[8 * p + 5] = b.x5;
+        S[8 * p + 6] = b.x6;
+        S[8 * p + 7] = b.x7;
+    }
 }
 
 // ShiftRows, then MixColumns (when MIX), then AddRoundKey with the plane masks
