@@ -168,16 +168,17 @@ def bitslice_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_bitsliced_ops():
-    """ALU lane-operations per 16-byte block of the AES-256 bitsliced kernel,
-    from the committed ncu record, if it was taken on the current sources."""
+def recorded_bitsliced():
+    """The committed ncu record of the AES-256 bitsliced kernel (ALU
+    lane-operations per 16-byte block, DRAM bytes of its 256 MiB capture), if
+    it was taken on the current sources (else an empty dict)."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "xts256_bitsliced_alu.json")))
     except (OSError, ValueError):
-        return None
+        return {}
     if rec.get("csrc_sha256") != bitslice_hash():
-        return None
-    return rec.get("alu_lane_ops_per_block")
+        return {}
+    return rec
 
 
 def measured_peaks():
@@ -251,6 +252,8 @@ def run_reference(args):
 
 def pct(lat_ns):
     a = np.sort(np.asarray(lat_ns, dtype=np.float64)) / 1e3
+    if not len(a):
+        return None
     q = lambda p: float(a[min(len(a) - 1, int(np.ceil(p / 100 * len(a))) - 1)])
     return {"p50_us": q(50), "p99_us": q(99), "p99.9_us": q(99.9), "max_us": float(a[-1])}
 
@@ -384,19 +387,23 @@ def run_serving(ctx, kg, dev, seconds, host=False):
         finally:
             ctx.serve_stop(30_000_000_000)
         d = detail.reshape(n, 3).astype(np.int64)
+        # device stamps lost to a slot that retired a later request before the
+        # host looked (0, 0) are left out of the device-service figures
+        stamped = (d[:, 1] > 0) & (d[:, 2] >= d[:, 1])
         service = d[:, 2] - d[:, 1]
         by_mode = {}
         for m, name in ((w.MODE_XTS, "xts"), (w.MODE_CBC_DEC, "cbc_dec"), (w.MODE_CBC_ENC, "cbc_enc")):
             sel = mix.modes == m
             if sel.any():
-                by_mode[name] = {"latency": pct(lat[sel]), "device_service": pct(service[sel])}
+                by_mode[name] = {"latency": pct(lat[sel]), "device_service": pct(service[sel & stamped])}
         with ClockSampler(dev) as clk_pr:
             rc2, lat2, wall2 = ctx.replay_launches(reqs, arr, nstreams=8, timeout_ns=120_000_000_000)
         total = int(mix.sizes.sum())
         res.append({
             "rate_req_s": rate, "requests": n, "offered_GB/s": total / (float(arr[-1]) / 1e9) / 1e9,
             "ring": {"GB/s": total / (wall / 1e9) / 1e9, "rc": rc, "latency": pct(lat),
-                     "host_wait_before_publish": pct(d[:, 0]), "device_service": pct(service),
+                     "host_wait_before_publish": pct(d[:, 0]), "device_service": pct(service[stamped]),
+                     "device_stamps_lost": int(n - stamped.sum()),
                      "by_mode": by_mode, "clocks": clk_ring.summary(),
                      "busy_refusals": stats["busy_refusals"], "launches": stats["launches"]},
             "per_request": {"GB/s": total / (wall2 / 1e9) / 1e9, "rc": rc2, "latency": pct(lat2),
@@ -744,7 +751,12 @@ def run_kgpu(args):
     if bitsliced:
         # ALU-bound: lane-operations of the ALU pipe per block (counted once with
         # ncu on this kernel) x blocks, against SMs x 64 lane-ops/clk x clock
-        rec = recorded_bitsliced_ops()
+        bs_rec = recorded_bitsliced()
+        rec = bs_rec.get("alu_lane_ops_per_block")
+        # DRAM traffic grows with the bytes processed: the 256 MiB capture
+        # scaled to this launch
+        cap = bs_rec.get("dram_bytes_per_launch_256mib")
+        traffic = cap * nbytes / (256 << 20) if cap else None
         alu_peak = props.multi_processor_count * ALU_LANE_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         achieved = rec * nblocks / launch_s / 1e12 if rec else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",

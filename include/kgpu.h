@@ -389,9 +389,11 @@ int kgpu_serve_submit_many(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kg
 /*
  * Wait for a served request.  timeout_ns: 0 = check once, < 0 = wait until
  * done, > 0 = wait at most that long.  KGPU_OK when complete (*status, if not
- * NULL: 0 or the request's KGPU_E* code; stamps, if not NULL: the device's
- * %globaltimer at its first tile and at its completion, 0 when the slot has
- * been reused since), KGPU_ETIMEDOUT while pending, KGPU_ENOENT for a ticket
+ * NULL: 0 or the request's KGPU_E* code -- codes of the newest 4096 failed
+ * requests are kept after their slots are reused; stamps, if not NULL: the
+ * device's %globaltimer at its first tile and at its completion, 0 when the
+ * slot has since retired a later request), KGPU_ETIMEDOUT while pending,
+ * KGPU_ENOENT for a ticket
  * that was never issued.  Relaunches the kernel if it exited with work pending.
  */
 int kgpu_serve_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *status, uint64_t *stamps);
@@ -415,7 +417,9 @@ int kgpu_serve_get_stats(kgpu_ctx *ctx, kgpu_serve_stats *out);
  * (their latency is then UINT64_MAX).  kgpu_replay_serve can also fill
  * detail[3 * i ...] (if not NULL) with: the time request i waited on the host
  * before it was published (ns, admission and ring limits included), and the
- * device's %globaltimer when its first tile started and when it completed.
+ * device's %globaltimer when its first tile started and when it completed
+ * (both 0 if the host saw the completion only after its slot had retired a
+ * later request too).
  */
 int kgpu_replay_serve(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
                       int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns, uint64_t *detail);

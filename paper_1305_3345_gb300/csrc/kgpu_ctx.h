@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <utility>
+#include <map>
 #include <vector>
 
 #include "kgpu_internal.h"
@@ -72,6 +73,12 @@ struct ServeState {
     std::vector<uint8_t> slot_busy;
     std::vector<uint64_t> slot_seq, slot_len;
     std::vector<uint64_t> outstanding;  // seqs published and not yet seen complete
+    // What the device reported for the last request each slot retired, copied
+    // when the host sees it complete -- always before the slot is staged again,
+    // which clears the mapped words -- so a late poller still finds it.
+    std::vector<uint64_t> ret_seq, ret_t_start, ret_t_done;
+    std::vector<int> ret_status;
+    std::map<uint64_t, int> failed;  // seq -> KGPU_E* of failed requests (the newest kFailedKept)
     uint64_t submitted = 0, completed = 0, busy_refusals = 0, launches = 0;
     uint64_t last_alive_check = 0;  // ns; publish re-checks the kernel at most every 20 us
     unsigned last_exit = 0;

@@ -133,6 +133,11 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     st.slot_busy.assign(S, 0);
     st.slot_seq.assign(S, 0);
     st.slot_len.assign(S, 0);
+    st.ret_seq.assign(S, UINT64_MAX);
+    st.ret_t_start.assign(S, 0);
+    st.ret_t_done.assign(S, 0);
+    st.ret_status.assign(S, 0);
+    st.failed.clear();
     st.outstanding.clear();
     st.outstanding.reserve(S);
     st.started = true;
@@ -167,12 +172,27 @@ int ensure_running(kgpu_ctx* ctx, ServeState& st) {
 }
 
 // Retire every outstanding request whose completion the device has published.
+// Failed requests whose codes are kept for kgpu_serve_poll after their slot
+// has been reused.
+constexpr size_t kFailedKept = 4096;
+
+// Retire every outstanding request the device has completed.  The slot's
+// status and stamps are the request's own here: the device wrote them before
+// its completion word, and the slot is not staged again before this runs.
 void reap(ServeState& st) {
     size_t w = 0;
     for (size_t i = 0; i < st.outstanding.size(); i++) {
         const uint64_t seq = st.outstanding[i];
         const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
         if (load_acquire(&st.done_seq[s]) >= seq + 1) {
+            st.ret_seq[s] = seq;
+            st.ret_status[s] = load_acquire(&st.status[s]);
+            st.ret_t_start[s] = load_acquire(&st.t_start[s]);
+            st.ret_t_done[s] = load_acquire(&st.t_done[s]);
+            if (st.ret_status[s]) {
+                st.failed[seq] = st.ret_status[s];
+                if (st.failed.size() > kFailedKept) st.failed.erase(st.failed.begin());
+            }
             st.slot_busy[s] = 0;
             st.inflight_bytes -= st.slot_len[s];
             st.completed++;
@@ -368,11 +388,18 @@ int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* 
     for (;;) {
         const unsigned long long d = load_acquire(&st.done_seq[s]);
         if (d >= seq + 1) {
-            const bool same = d == seq + 1;
-            if (status) *status = same ? load_acquire(&st.status[s]) : 0;
+            // complete: read what reap retired (the slot may be in use again)
+            std::lock_guard<std::mutex> lk(ctx->serve_mu);
+            if (!st.started) return KGPU_ENOENT;
+            reap(st);
+            const bool kept = st.ret_seq[s] == seq;
+            if (status) {
+                auto f = st.failed.find(seq);
+                *status = kept ? st.ret_status[s] : (f != st.failed.end() ? f->second : 0);
+            }
             if (stamps) {
-                stamps[0] = same ? load_acquire(&st.t_start[s]) : 0;
-                stamps[1] = same ? load_acquire(&st.t_done[s]) : 0;
+                stamps[0] = kept ? st.ret_t_start[s] : 0;
+                stamps[1] = kept ? st.ret_t_done[s] : 0;
             }
             return KGPU_OK;
         }
@@ -484,21 +511,20 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
         std::vector<size_t> pending;
         size_t seen = 0, done = 0;
         uint64_t last_check = now_ns();
+        std::vector<size_t> fresh;
         while (done < n) {
             const size_t p = produced.load(std::memory_order_acquire);
             while (seen < p) pending.push_back(seen++);
             size_t w = 0;
             const uint64_t t = now_ns();
+            fresh.clear();
             for (size_t k = 0; k < pending.size(); k++) {
                 const size_t i = pending[k];
                 const uint64_t seq = seq_of[i].load(std::memory_order_acquire);
                 const uint32_t slot = (uint32_t)(seq & (nslots - 1));
                 if (load_acquire(&st.done_seq[slot]) >= seq + 1) {
                     latency_ns[i] = t - (t0 + arrival_ns[i]);
-                    if (detail) {  // the stamps stay valid until the slot is reused
-                        detail[3 * i + 1] = load_acquire(&st.t_start[slot]);
-                        detail[3 * i + 2] = load_acquire(&st.t_done[slot]);
-                    }
+                    fresh.push_back(i);
                     last_done = t;
                     done++;
                 } else {
@@ -506,6 +532,19 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
                 }
             }
             pending.resize(w);
+            if (detail && !fresh.empty()) {
+                // the device's stamps as reap retired them; 0, 0 when the
+                // slot has since retired a later request as well
+                std::lock_guard<std::mutex> lk(ctx->serve_mu);
+                reap(st);
+                for (size_t i : fresh) {
+                    const uint64_t seq = seq_of[i].load(std::memory_order_relaxed);
+                    const uint32_t slot = (uint32_t)(seq & (nslots - 1));
+                    const bool kept = st.ret_seq[slot] == seq;
+                    detail[3 * i + 1] = kept ? st.ret_t_start[slot] : 0;
+                    detail[3 * i + 2] = kept ? st.ret_t_done[slot] : 0;
+                }
+            }
             if (t - last_check > 100000) {  // relaunch the kernel if it exited with work pending
                 std::lock_guard<std::mutex> lk(ctx->serve_mu);
                 if (!pending.empty() && ensure_running(ctx, st)) error.store(KGPU_EIO);

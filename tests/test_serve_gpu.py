@@ -305,3 +305,42 @@ def test_serve_submit_many_bursts(ctx):
     for i in range(len(t.reqs)):
         assert np.array_equal(t.got(i), t.expected(i)), (i, int(t.modes[i]))
     t.close()
+
+
+def test_serve_stamps_survive_slot_reuse(ctx):
+    """An 8-slot ring cycles each slot many times before the first tickets are
+    polled: every poll still returns status 0 and either the request's own
+    device stamps (start > 0, done >= start) or (0, 0) once its slot has
+    retired a later request -- never another request's or half-cleared
+    stamps -- and the last ring's worth of tickets keep theirs.  The trace
+    replay on the same small ring gives the same guarantee for its detail."""
+    t = Traffic(ctx, seed=79, n=96, lo=4096, hi=64 << 10, nkeys=4)
+    ctx.serve_start(ring_slots=8)
+    try:
+        tickets, k = [], 0
+        while k < len(t.reqs):
+            rc, tk = ctx.serve_submit_many(t.array(which=0)[k:])
+            tickets += [int(x) for x in tk]
+            k += len(tk)
+        seen = []
+        for tk in tickets:
+            rc, st, stamps = ctx.serve_poll(tk, 10_000_000_000)
+            assert rc == 0 and st == 0
+            s0, s1 = int(stamps[0]), int(stamps[1])
+            assert (s0, s1) == (0, 0) or s1 >= s0 > 0, (tk, s0, s1)
+            seen.append((s0, s1))
+        assert all(s[0] > 0 for s in seen[-8:])
+        arr = np.cumsum(np.full(len(t.reqs), 200, dtype=np.uint64))   # 5M requests/s: overload
+        detail = np.zeros(3 * len(t.reqs), dtype=np.uint64)
+        rc, lat, wall = ctx.replay_serve(t.array(which=1), arr, 20_000_000_000, detail=detail)
+        assert rc == 0
+        d = detail.reshape(-1, 3).astype(np.int64)
+        ok = ((d[:, 1] == 0) & (d[:, 2] == 0)) | ((d[:, 1] > 0) & (d[:, 2] >= d[:, 1]))
+        assert ok.all(), d[~ok][:4]
+        assert (d[:, 1] > 0).sum() >= 8
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    for i in range(len(t.reqs)):
+        assert np.array_equal(t.got(i, 0), t.expected(i)), i
+        assert np.array_equal(t.got(i, 1), t.expected(i)), i
+    t.close()
