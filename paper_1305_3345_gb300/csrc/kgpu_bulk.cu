@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) cbc_enc_kernel(const __grid_c
 constexpr int kStageBlocks = 8;
 constexpr int kStageRow = kStageBlocks * 16 + 16;  // one page's 8 blocks, padded against bank conflicts
 constexpr int kStageWarpBytes = 32 * kStageRow;
+static_assert(kStageWarpBytes == kStageWarpSmem, "staging area size");
 
 template <int NR>
 __global__ void __launch_bounds__(kCbcEncStagedThreads, 1) cbc_enc_staged_kernel(const __grid_constant__ CbcParams p) {
@@ -590,13 +591,46 @@ cudaError_t launch_xts_cts(const CtsParams& p, int nr, int dir, int num_sms, cud
     return cudaGetLastError();
 }
 
+// A group (32 whole-page chains, one warp) is one long serial job, so the
+// groups run in waves of warps x SMs, and a last wave that fills only part of
+// the warps leaves the SMs' lookup path under-used for a whole chain's time.
+// With 16 warps an SM's shared-memory path is kept busy (ncu: 91% of the
+// kernel's own lookup bound, the rest being the tail), so a wave of w warps
+// per SM costs about max(w, 16) chain-times of lookups.  Pick the warp count
+// with the lowest total over the waves (ties: more warps).  1 GiB of 4-KiB
+// pages is 8,192 groups: 16 warps take 3.37 waves (the fourth on 37% of the
+// warps), 18 take 2.99.  (At 21 warps the register cap drops to 80 and the
+// kernel spills.)
+int cbc_enc_staged_warps(uint64_t groups, int num_sms) {
+    constexpr int kSat = 16;
+    const uint64_t sms = (uint64_t)(num_sms > 0 ? num_sms : 1);
+    if (groups < kSat * sms) {  // one wave; extra warps only speed the table fill
+        const uint64_t w = (groups + sms - 1) / sms;
+        return (int)(w < 8 ? 8 : w);
+    }
+    int best = kCbcEncStagedMaxWarps;
+    uint64_t best_cost = UINT64_MAX;
+    for (int w = kCbcEncStagedMaxWarps; w >= kSat; --w) {
+        const uint64_t per_wave = (uint64_t)w * sms;
+        const uint64_t full = groups / per_wave, rest = groups % per_wave;
+        const uint64_t last = (rest + sms - 1) / sms;  // warps per SM in the last wave
+        const uint64_t cost = full * (uint64_t)w + (rest ? (last > kSat ? last : kSat) : 0);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = w;
+        }
+    }
+    return best;
+}
+
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
     if (p.bpp % kStageBlocks == 0) {
         auto fn = cbc_enc_staged_fn(nr);
         if (!fn) return cudaErrorInvalidValue;
         const uint64_t groups = (p.npages + 31) / 32;
         const int grid = (int)(groups < (uint64_t)num_sms ? (groups ? groups : 1) : num_sms);
-        fn<<<grid, kCbcEncStagedThreads, kSmemEncStaged, s>>>(p);
+        const int warps = cbc_enc_staged_warps(groups, num_sms);
+        fn<<<grid, warps * 32, kSmemEnc + warps * kStageWarpSmem, s>>>(p);
         return cudaGetLastError();
     }
     auto fn = cbc_fn(nr, true);

@@ -20,10 +20,18 @@ constexpr size_t kSmemDec = 3 * kRegionBytes;  // regions A, B, C
 // Threads per CTA of the bulk kernels (one CTA per SM).
 constexpr int kBulkThreads = 1024;
 
-// Staged CBC encryption: 16 warps per CTA, each with a 32-page x 8-block
-// staging area (4608 B) after the two table regions.
-constexpr int kCbcEncStagedThreads = 512;
-constexpr size_t kSmemEncStaged = kSmemEnc + (kCbcEncStagedThreads / 32) * 4608;
+// Staged CBC encryption: up to 20 warps per CTA (96 registers a thread), each
+// with a 32-page x 8-block staging area (4608 B) after the two table regions.
+// The launch picks the warp count for the page count (cbc_enc_staged_warps).
+constexpr int kCbcEncStagedMaxWarps = 20;
+constexpr int kCbcEncStagedThreads = kCbcEncStagedMaxWarps * 32;
+constexpr size_t kStageWarpSmem = 4608;
+constexpr size_t kSmemEncStaged = kSmemEnc + kCbcEncStagedMaxWarps * kStageWarpSmem;
+static_assert(kSmemEncStaged <= 232448, "staged CBC encryption exceeds the 227-KB shared-memory limit");
+
+// Warps per CTA of the staged CBC-encryption launch for `groups` groups of 32
+// pages on num_sms SMs (one CTA per SM).
+int cbc_enc_staged_warps(uint64_t groups, int num_sms);
 
 // Where dynamic shared memory starts in a CTA's shared window (the reserved
 // system area comes first); the kernels fold it into their load offsets.

@@ -73,9 +73,14 @@ struct ServeState {
     std::vector<uint8_t> slot_busy;
     std::vector<uint64_t> slot_seq, slot_len;
     std::vector<uint64_t> outstanding;  // seqs published and not yet seen complete
+    // slot_gen[s]: the seq staged in slot s, UINT64_MAX while stage() clears
+    // the slot's mapped status and stamps -- a sequence lock that lets readers
+    // without serve_mu tell whether what they read is still their request's.
+    std::vector<uint64_t> slot_gen;
     // What the device reported for the last request each slot retired, copied
-    // when the host sees it complete -- always before the slot is staged again,
-    // which clears the mapped words -- so a late poller still finds it.
+    // by reap -- always before the slot is staged again -- so a late reader
+    // still finds it.  ret_seq[s] is the record's sequence lock (UINT64_MAX
+    // while reap rewrites it).
     std::vector<uint64_t> ret_seq, ret_t_start, ret_t_done;
     std::vector<int> ret_status;
     std::map<uint64_t, int> failed;  // seq -> KGPU_E* of failed requests (the newest kFailedKept)

@@ -133,6 +133,7 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     st.slot_busy.assign(S, 0);
     st.slot_seq.assign(S, 0);
     st.slot_len.assign(S, 0);
+    st.slot_gen.assign(S, UINT64_MAX);
     st.ret_seq.assign(S, UINT64_MAX);
     st.ret_t_start.assign(S, 0);
     st.ret_t_done.assign(S, 0);
@@ -185,12 +186,15 @@ void reap(ServeState& st) {
         const uint64_t seq = st.outstanding[i];
         const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
         if (load_acquire(&st.done_seq[s]) >= seq + 1) {
-            st.ret_seq[s] = seq;
-            st.ret_status[s] = load_acquire(&st.status[s]);
-            st.ret_t_start[s] = load_acquire(&st.t_start[s]);
-            st.ret_t_done[s] = load_acquire(&st.t_done[s]);
-            if (st.ret_status[s]) {
-                st.failed[seq] = st.ret_status[s];
+            const int code = load_acquire(&st.status[s]);
+            __atomic_store_n(&st.ret_seq[s], UINT64_MAX, __ATOMIC_RELAXED);
+            __atomic_thread_fence(__ATOMIC_RELEASE);
+            __atomic_store_n(&st.ret_status[s], code, __ATOMIC_RELAXED);
+            __atomic_store_n(&st.ret_t_start[s], (uint64_t)load_acquire(&st.t_start[s]), __ATOMIC_RELAXED);
+            __atomic_store_n(&st.ret_t_done[s], (uint64_t)load_acquire(&st.t_done[s]), __ATOMIC_RELAXED);
+            __atomic_store_n(&st.ret_seq[s], seq, __ATOMIC_RELEASE);
+            if (code) {
+                st.failed[seq] = code;
                 if (st.failed.size() > kFailedKept) st.failed.erase(st.failed.begin());
             }
             st.slot_busy[s] = 0;
@@ -201,6 +205,38 @@ void reap(ServeState& st) {
         }
     }
     st.outstanding.resize(w);
+}
+
+// The device's status and stamps for request seq, which the caller has seen
+// complete (done_seq of its slot >= seq + 1, acquire), without serve_mu: from
+// the slot's mapped words while the slot still holds seq, else from reap's
+// record of it.  false when the slot has since retired a later request too.
+bool read_completed(const ServeState& st, uint64_t seq, int* status, uint64_t* t_start, uint64_t* t_done) {
+    const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
+    if (__atomic_load_n(&st.slot_gen[s], __ATOMIC_ACQUIRE) == seq) {
+        const int c = load_acquire(&st.status[s]);
+        const uint64_t a = load_acquire(&st.t_start[s]), b = load_acquire(&st.t_done[s]);
+        __atomic_thread_fence(__ATOMIC_ACQUIRE);
+        if (__atomic_load_n(&st.slot_gen[s], __ATOMIC_RELAXED) == seq) {
+            *status = c;
+            *t_start = a;
+            *t_done = b;
+            return true;
+        }
+    }
+    if (__atomic_load_n(&st.ret_seq[s], __ATOMIC_ACQUIRE) == seq) {
+        const int c = __atomic_load_n(&st.ret_status[s], __ATOMIC_RELAXED);
+        const uint64_t a = __atomic_load_n(&st.ret_t_start[s], __ATOMIC_RELAXED);
+        const uint64_t b = __atomic_load_n(&st.ret_t_done[s], __ATOMIC_RELAXED);
+        __atomic_thread_fence(__ATOMIC_ACQUIRE);
+        if (__atomic_load_n(&st.ret_seq[s], __ATOMIC_RELAXED) == seq) {
+            *status = c;
+            *t_start = a;
+            *t_done = b;
+            return true;
+        }
+    }
+    return false;
 }
 
 // Publish a validated descriptor.  Caller holds serve_mu.
@@ -247,9 +283,13 @@ int stage(ServeState& st, const ReqDesc& dreq, uint64_t* seq_out) {
     sl.d = d;
     sl.ntiles = nt;
     sl.seq = seq;
-    st.status[s] = 0;
-    st.t_start[s] = 0;
-    st.t_done[s] = 0;
+    // clear the slot's mapped words inside the generation's sequence lock
+    __atomic_store_n(&st.slot_gen[s], UINT64_MAX, __ATOMIC_RELAXED);
+    __atomic_thread_fence(__ATOMIC_RELEASE);
+    __atomic_store_n(&st.status[s], 0, __ATOMIC_RELAXED);
+    __atomic_store_n(&st.t_start[s], 0ull, __ATOMIC_RELAXED);
+    __atomic_store_n(&st.t_done[s], 0ull, __ATOMIC_RELAXED);
+    __atomic_store_n(&st.slot_gen[s], seq, __ATOMIC_RELEASE);
     st.slot_busy[s] = 1;
     st.slot_seq[s] = seq;
     st.slot_len[s] = len;
@@ -388,18 +428,20 @@ int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* 
     for (;;) {
         const unsigned long long d = load_acquire(&st.done_seq[s]);
         if (d >= seq + 1) {
-            // complete: read what reap retired (the slot may be in use again)
-            std::lock_guard<std::mutex> lk(ctx->serve_mu);
-            if (!st.started) return KGPU_ENOENT;
-            reap(st);
-            const bool kept = st.ret_seq[s] == seq;
-            if (status) {
+            int code = 0;
+            uint64_t a = 0, b = 0;
+            if (!read_completed(st, seq, &code, &a, &b)) {
+                // its slot has retired a later request too: stamps are gone,
+                // a failure code is kept by ticket
+                std::lock_guard<std::mutex> lk(ctx->serve_mu);
                 auto f = st.failed.find(seq);
-                *status = kept ? st.ret_status[s] : (f != st.failed.end() ? f->second : 0);
+                code = f != st.failed.end() ? f->second : 0;
+                a = b = 0;
             }
+            if (status) *status = code;
             if (stamps) {
-                stamps[0] = kept ? st.ret_t_start[s] : 0;
-                stamps[1] = kept ? st.ret_t_done[s] : 0;
+                stamps[0] = a;
+                stamps[1] = b;
             }
             return KGPU_OK;
         }
@@ -511,20 +553,24 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
         std::vector<size_t> pending;
         size_t seen = 0, done = 0;
         uint64_t last_check = now_ns();
-        std::vector<size_t> fresh;
         while (done < n) {
             const size_t p = produced.load(std::memory_order_acquire);
             while (seen < p) pending.push_back(seen++);
             size_t w = 0;
             const uint64_t t = now_ns();
-            fresh.clear();
             for (size_t k = 0; k < pending.size(); k++) {
                 const size_t i = pending[k];
                 const uint64_t seq = seq_of[i].load(std::memory_order_acquire);
                 const uint32_t slot = (uint32_t)(seq & (nslots - 1));
                 if (load_acquire(&st.done_seq[slot]) >= seq + 1) {
                     latency_ns[i] = t - (t0 + arrival_ns[i]);
-                    fresh.push_back(i);
+                    if (detail) {  // 0, 0 once the slot has retired a later request too
+                        int code = 0;
+                        uint64_t a = 0, b = 0;
+                        if (!read_completed(st, seq, &code, &a, &b)) a = b = 0;
+                        detail[3 * i + 1] = a;
+                        detail[3 * i + 2] = b;
+                    }
                     last_done = t;
                     done++;
                 } else {
@@ -532,23 +578,15 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
                 }
             }
             pending.resize(w);
-            if (detail && !fresh.empty()) {
-                // the device's stamps as reap retired them; 0, 0 when the
-                // slot has since retired a later request as well
-                std::lock_guard<std::mutex> lk(ctx->serve_mu);
-                reap(st);
-                for (size_t i : fresh) {
-                    const uint64_t seq = seq_of[i].load(std::memory_order_relaxed);
-                    const uint32_t slot = (uint32_t)(seq & (nslots - 1));
-                    const bool kept = st.ret_seq[slot] == seq;
-                    detail[3 * i + 1] = kept ? st.ret_t_start[slot] : 0;
-                    detail[3 * i + 2] = kept ? st.ret_t_done[slot] : 0;
-                }
-            }
             if (t - last_check > 100000) {  // relaunch the kernel if it exited with work pending
-                std::lock_guard<std::mutex> lk(ctx->serve_mu);
-                if (!pending.empty() && ensure_running(ctx, st)) error.store(KGPU_EIO);
-                last_check = t;
+                // While the producer still publishes it checks the kernel itself,
+                // and holds the mutex most of the time when the ring is full: do
+                // not queue behind it, or completions go unseen meanwhile.
+                std::unique_lock<std::mutex> lk(ctx->serve_mu, std::defer_lock);
+                if (produced.load(std::memory_order_acquire) < n ? lk.try_lock() : (lk.lock(), true)) {
+                    if (!pending.empty() && ensure_running(ctx, st)) error.store(KGPU_EIO);
+                    last_check = t;
+                }
             }
             if (abort.load() || error.load() || t > deadline) break;
         }

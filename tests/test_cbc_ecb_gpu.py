@@ -50,6 +50,23 @@ def test_cbc_vs_oracle(ctx, bits, page, npages):
         assert np.array_equal(got, ref), (bits, page, npages, enc)
 
 
+@pytest.mark.parametrize("page,npages", [
+    (128, 1217 * 32 + 3),     # 1,218 groups of 32 pages: one wave of 9 warps per CTA, ragged last group
+    (128, 8192 * 32 + 5),     # 8,193 groups: several waves, the warp count set by the tail, ragged last group
+    (256, 100003),            # 3,126 groups, 16 blocks a page
+])
+def test_cbc_encrypt_launch_shapes(ctx, page, npages):
+    """CBC encryption of many short pages: the staged kernel's warp count per
+    CTA follows the number of 32-page groups (one wave, or waves sized to
+    leave no small last wave), so these sizes cover each choice."""
+    key = w.single_key(13, 128)
+    data = w.seeded_bytes(13 + page, w.STREAM_DATA, page * npages)
+    ivs = w.page_ivs(13 + page, npages)
+    ref = oracle.cbc(key, 0, data, page, ivs)
+    got = run_cbc(ctx, key, True, data, page, ivs)
+    assert np.array_equal(got, ref), (page, npages)
+
+
 def test_cbc_in_place(ctx):
     key = w.single_key(13, 128)
     data = w.seeded_bytes(13, w.STREAM_DATA, 4096 * 500)
