@@ -182,6 +182,10 @@ int kgpu_aes_ecb_crypt(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, vo
  * HOST pointers (pinned memory gives full link speed; pageable memory works
  * but is slower); src == dst is allowed.  Blocks until dst holds the result.
  * Device staging buffers are owned by the context and reused across calls.
+ * When both [src, src + len) and [dst, dst + len) lie inside ranges
+ * registered with kgpu_host_register, there is no staging and no copy: the
+ * kernel reads and writes the host pages in place over the host link, and
+ * chunk_bytes is ignored.  kgpu_host_unregister waits for such a call.
  */
 int kgpu_aes_xts_crypt_host(kgpu_ctx *ctx, kgpu_key key, int dir, const void *src, void *dst, size_t len,
                             size_t du_size, uint64_t first_sector, size_t chunk_bytes);

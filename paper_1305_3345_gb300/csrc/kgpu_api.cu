@@ -263,13 +263,14 @@ int kgpu_host_unregister(kgpu_ctx* ctx, void* ptr) {
         std::lock_guard<std::mutex> lk(ctx->hreg_mu);
         if (find() == ctx->hreg.end()) return KGPU_ENOENT;
     }
-    // batches in flight and requests on the serving ring may still read or
-    // write the range
+    // batches in flight, requests on the serving ring and a host-buffer call
+    // (it holds host_mu throughout) may still read or write the range
     int rc = batches_quiesce(ctx);
     if (!rc) rc = serve_quiesce(ctx, 60000000000ll);
     if (rc) return rc;
     HostRange r;
     {
+        std::lock_guard<std::mutex> hk(ctx->host_mu);
         std::lock_guard<std::mutex> lk(ctx->hreg_mu);
         auto it = find();
         if (it == ctx->hreg.end()) return KGPU_ENOENT;
@@ -436,11 +437,24 @@ int kgpu_aes_xts_crypt_host(kgpu_ctx* ctx, kgpu_key key, int dir, const void* sr
     chunk -= chunk % du_size;
     if (chunk > len) chunk = len;
 
+    // held for the whole call: kgpu_host_unregister takes it before it unpins
     std::lock_guard<std::mutex> lk(ctx->host_mu);
     DeviceGuard g(ctx->device);
     for (int i = 0; i < kgpu_ctx::kStages; i++) {
         if (!ctx->hs[i] && cudaStreamCreateWithFlags(&ctx->hs[i], cudaStreamNonBlocking) != cudaSuccess)
             return KGPU_EIO;
+    }
+    // Both buffers in registered ranges: the kernel works on the host pages in
+    // place over the coherent link, at the link's speed in both directions at
+    // once, with no staging and no pipeline fill or drain.
+    uintptr_t hsrc = 0, hdst = 0;
+    if (host_translate(ctx, src, len, &hsrc) == KGPU_OK && host_translate(ctx, dst, len, &hdst) == KGPU_OK) {
+        BulkParams p;
+        fill_bulk(&p, k, dir, reinterpret_cast<const void*>(hsrc), reinterpret_cast<void*>(hdst), len, du_size,
+                  first_sector);
+        cudaError_t e = launch_xts(p, k.nr, dir, ctx->num_sms, ctx->hs[0]);
+        cudaError_t e2 = cudaStreamSynchronize(ctx->hs[0]);
+        return from_cuda(e != cudaSuccess ? e : e2);
     }
     if (ctx->staging_bytes < chunk) {
         for (int i = 0; i < kgpu_ctx::kStages; i++) {

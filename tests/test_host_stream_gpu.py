@@ -42,3 +42,34 @@ def test_host_stream_rejects_device_pointer(ctx):
     d = torch.zeros(4096, dtype=torch.uint8, device="cuda")
     assert kg.lib().kgpu_aes_xts_crypt_host(ctx.handle, kh, 0, d.data_ptr(), d.data_ptr(), 4096, 4096, 0, 0) == -14
     ctx.delkey(kh)
+
+
+@pytest.mark.parametrize("bits,du", [(256, 4096), (128, 512)])
+def test_host_call_on_registered_pages_in_place_over_the_link(ctx, bits, du):
+    """Both buffers registered: the call runs the kernel on the host pages
+    directly (no staging).  Out of place, in place and decryption must equal
+    the oracle; with only one buffer registered the call takes the copy
+    pipeline and gives the same bytes; unregistering afterwards succeeds."""
+    import torch
+    key = w.xts_key(19 + bits, bits)
+    n = du * 3001
+    data = w.seeded_bytes(19 + du, w.STREAM_DATA, n)
+    src = torch.from_numpy(data.copy()).pin_memory()
+    dst = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    other = torch.zeros(n, dtype=torch.uint8).pin_memory()
+    kh = ctx.setkey(key, True)
+    ref = oracle.xts(key, 0, data, du, 2**40 + 3)
+    ctx.host_register(src)
+    ctx.host_register(dst)
+    try:
+        ctx.xts_crypt_host(kh, 0, src, dst, du, 2**40 + 3, 0)
+        assert np.array_equal(dst.numpy(), ref)
+        ctx.xts_crypt_host(kh, 0, src, other, du, 2**40 + 3, 1 << 20)   # dst not registered: pipeline
+        assert np.array_equal(other.numpy(), ref)
+        ctx.xts_crypt_host(kh, 1, dst, dst, du, 2**40 + 3, 0)           # in place, registered
+        assert np.array_equal(dst.numpy(), data)
+    finally:
+        ctx.host_unregister(src)
+        ctx.host_unregister(dst)
+    ctx.delkey(kh)
+
