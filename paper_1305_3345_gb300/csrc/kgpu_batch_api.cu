@@ -44,7 +44,7 @@ int tuning_ok(const kgpu_tuning* t) {
 // Validate all requests and pack header | descriptors | tile prefix into buf
 // (which must hold batch_bytes(n)).  Returns the first error, with every
 // request's own code in req_status when given.
-int pack_batch(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, uint32_t tile_chunks, uint8_t* buf,
+int pack_batch(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, uint32_t tile_chunks, uint64_t warps, uint8_t* buf,
                int* req_status) {
     RangeCache rc;
     int first = KGPU_OK;
@@ -58,7 +58,7 @@ int pack_batch(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, uint32_t tile_
         if (r) descs[i].nblocks = 0;  // refused: no tiles
     }
     const uint64_t tiles = order_batch(descs, (uint32_t)n, [&](uint32_t i) { return descs[i].nblocks == 0; },
-                                       prefix, order);
+                                       2 * warps, prefix, order);
     BatchHeader* h = reinterpret_cast<BatchHeader*>(buf);
     h->total_tiles = tiles;
     h->nreq = (uint32_t)n;
@@ -302,7 +302,7 @@ int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream s
     s.issued = false;
     int rc = prepare_slot(ctx, s, n ? n : 1, t);
     if (rc) return rc;
-    rc = pack_batch(ctx, reqs, n, t.tile_chunks, s.h_buf, req_status);
+    rc = pack_batch(ctx, reqs, n, t.tile_chunks, (uint64_t)t.ctas * (t.threads / 32), s.h_buf, req_status);
     if (rc) return rc;
     s.nreq = (uint32_t)n;
     s.gen = ticket;
@@ -436,13 +436,14 @@ int kgpu_autotune(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream
     float chosen_ms = -1.f;
     for (uint32_t tc : tile_opts) {
         if (rc) break;
-        rc = pack_batch(ctx, reqs, n, tc, hbuf.data(), nullptr);
-        if (rc) break;
-        if (cudaMemcpy(dbuf, hbuf.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-            rc = KGPU_EIO;
-            break;
-        }
         for (uint32_t th : thread_opts) {
+            // the run order's tail reserve depends on the warp count
+            rc = pack_batch(ctx, reqs, n, tc, (uint64_t)ctx->num_sms * (th / 32), hbuf.data(), nullptr);
+            if (rc) break;
+            if (cudaMemcpy(dbuf, hbuf.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+                rc = KGPU_EIO;
+                break;
+            }
             BatchArgs a{};
             a.buf = dbuf;
             a.keys = ctx->d_keys;

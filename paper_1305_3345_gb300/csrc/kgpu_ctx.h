@@ -384,22 +384,65 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
 
 
 // Run order and tile prefix of a packed batch (descs already written; codes[i]
-// nonzero marks request i refused, which contributes no tiles).  CBC-encryption
-// requests run first: each of their tiles is 32 serial chains of a page's
-// blocks, several times longer than any other tile, and handed out last they
-// would run alone at the end of the batch (the longest-first rule for
-// scheduling independent jobs).  Returns the total tile count.
+// nonzero marks request i refused, which contributes no tiles).
+//
+// A request's latency inside a batch is the time until its last tile is done,
+// and tiles are handed out in run order, so requests run smallest first (the
+// shortest-processing-time rule, which minimises the mean completion time):
+// the many small requests of a mixed batch finish early instead of wherever
+// the caller happened to put them.  Where a request sits does not move the
+// batch's end as long as the last tiles handed out are short: XTS, ECB and
+// CBC-decryption tiles are all about one tile of work, but a CBC-encryption
+// tile is 32 serial chains of a page's blocks, several times longer, and one
+// handed out last runs alone at the end.  So every CBC-encryption request
+// runs before the tail reserve, the largest other requests holding their
+// last reserve_tiles tiles (two per resident warp: enough short work to keep
+// every warp busy while the long tiles finish).  Ties keep submission order.
+// Allocation-free.  Returns the total tile count.
 template <class Codes>
-uint64_t order_batch(const ReqDesc* descs, uint32_t n, const Codes& codes, uint64_t* prefix, uint32_t* order) {
-    uint32_t k = 0;
-    for (uint32_t pass = 0; pass < 2; pass++)
-        for (uint32_t i = 0; i < n; i++)
-            if ((descs[i].mode == KGPU_MODE_CBC_ENC) == (pass == 0)) order[k++] = i;
+uint64_t order_batch(const ReqDesc* descs, uint32_t n, const Codes& codes, uint64_t reserve_tiles, uint64_t* prefix,
+                     uint32_t* order) {
+    auto tiles_of = [&](uint32_t i) -> uint64_t {
+        return codes(i) ? 0 : (request_units(descs[i]) + descs[i].tile_units - 1) / descs[i].tile_units;
+    };
+    auto cbc_enc = [&](uint32_t i) { return descs[i].mode == KGPU_MODE_CBC_ENC; };
+    // 1. fewest tiles first, ties in submission order.  prefix[0, n) holds
+    // each request's tiles meanwhile.  Tile counts are usually small, and
+    // then a counting sort (stable by construction) does it in one pass;
+    // otherwise an in-place comparison sort on (tiles, index).
+    constexpr uint32_t kBuckets = 1024;
+    uint64_t max_tiles = 0;
+    for (uint32_t i = 0; i < n; i++) {
+        prefix[i] = tiles_of(i);
+        max_tiles = std::max(max_tiles, prefix[i]);
+    }
+    if (max_tiles < kBuckets) {
+        uint32_t start[kBuckets + 1] = {};
+        for (uint32_t i = 0; i < n; i++) start[prefix[i] + 1]++;
+        for (uint32_t b = 0; b < kBuckets; b++) start[b + 1] += start[b];
+        for (uint32_t i = 0; i < n; i++) order[start[prefix[i]]++] = i;
+    } else {  // a request of 1,024 tiles or more
+        for (uint32_t i = 0; i < n; i++) order[i] = i;
+        std::sort(order, order + n,
+                  [&](uint32_t a, uint32_t b) { return prefix[a] != prefix[b] ? prefix[a] < prefix[b] : a < b; });
+    }
+    // 2. the tail reserve order[r, n): its CBC-encryption requests move in
+    // front of the rest, both groups keeping their order
+    uint32_t r = n;
+    for (uint64_t held = 0; r > 0 && held < reserve_tiles; --r)
+        if (!cbc_enc(order[r - 1])) held += prefix[order[r - 1]];
+    uint32_t w = r;
+    for (uint32_t j = r; j < n; j++)  // prefix[r, n) is free from here: the staging area
+        prefix[j] = order[j];
+    for (uint32_t j = r; j < n; j++)
+        if (cbc_enc((uint32_t)prefix[j])) order[w++] = (uint32_t)prefix[j];
+    for (uint32_t j = r; j < n; j++)
+        if (!cbc_enc((uint32_t)prefix[j])) order[w++] = (uint32_t)prefix[j];
+    // 3. exclusive prefix of tiles in run order
     uint64_t tiles = 0;
     for (uint32_t j = 0; j < n; j++) {
-        const uint32_t i = order[j];
         prefix[j] = tiles;
-        if (!codes(i)) tiles += (request_units(descs[i]) + descs[i].tile_units - 1) / descs[i].tile_units;
+        tiles += tiles_of(order[j]);
     }
     prefix[n] = tiles;
     return tiles;

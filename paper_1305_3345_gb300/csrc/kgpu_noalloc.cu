@@ -114,7 +114,8 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
         if (r && !first) first = r;
     }
     if (first) return first;
-    const uint64_t tiles = order_batch(descs, (uint32_t)n, [](uint32_t) { return false; }, prefix, order);
+    const uint64_t tiles = order_batch(descs, (uint32_t)n, [](uint32_t) { return false; },
+                                       2 * (uint64_t)ctas * (threads / 32), prefix, order);
     BatchHeader* h = reinterpret_cast<BatchHeader*>(g_pack);
     h->total_tiles = tiles;
     h->nreq = (uint32_t)n;
