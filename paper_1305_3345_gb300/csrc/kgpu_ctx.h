@@ -377,7 +377,7 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
     d->key = q.key - 1;
     d->mode = q.mode;
     d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : q.dir;
-    d->host = ((q.flags & KGPU_REQ_SRC_HOST) ? kDescSrcHost : 0u) | ((q.flags & KGPU_REQ_DST_HOST) ? kDescDstHost : 0u);
+    d->flags = ((q.flags & KGPU_REQ_SRC_HOST) ? kDescSrcHost : 0u) | ((q.flags & KGPU_REQ_DST_HOST) ? kDescDstHost : 0u);
     set_tile_units(*d, tile_chunks);
     return KGPU_OK;
 }

@@ -54,11 +54,13 @@ struct ReqDesc {
     uint32_t mode;          // KGPU_MODE_*
     uint32_t dir;           // KGPU_ENCRYPT / KGPU_DECRYPT (XTS, ECB)
     uint32_t tile_units;    // work units (32-block chunks or pages) per tile
-    uint32_t host;          // kDescSrcHost | kDescDstHost: buffers in registered host memory
+    uint32_t flags;         // kDesc* below
 };
 static_assert(sizeof(ReqDesc) == 64, "descriptor layout");
-constexpr uint32_t kDescSrcHost = 1u;
-constexpr uint32_t kDescDstHost = 2u;
+constexpr uint32_t kDescSrcHost = 1u;  // source in registered host memory
+constexpr uint32_t kDescDstHost = 2u;  // destination in registered host memory
+constexpr uint32_t kDescQuad = 4u;     // CBC encryption, four lanes per page: tiles of kQuadPages pages
+constexpr uint32_t kQuadPages = 8;
 
 // Per-warp device scratch of the unified kernels: CBC encryption of
 // host-resident pages moves 8 blocks of each of a warp's 32 pages through it

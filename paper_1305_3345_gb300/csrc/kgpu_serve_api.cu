@@ -251,8 +251,10 @@ constexpr uint32_t kBacklogTileChunks = 64;  // 32 KiB
 // it gets 32-KiB tiles: per tile the workers claim a position, reload a key
 // schedule and (for XTS) run a 32-unit tweak batch, and on small tiles those
 // costs cap the ring's throughput.  A ring that keeps up keeps the configured
-// (default 2-KiB) tiles and their lower latency.  The check is one load of a
-// completion word, whatever the number of requests in flight.
+// (default 2-KiB) tiles and their lower latency, and runs CBC encryption of
+// device pages four lanes to a page (twice the chain speed, a quarter of the
+// pages per warp).  The check is one load of a completion word, whatever the
+// number of requests in flight.
 bool backlogged(const ServeState& st) {
     const uint64_t q = st.nslots / 4;
     if (st.next_seq < q) return false;
@@ -262,7 +264,14 @@ bool backlogged(const ServeState& st) {
 
 int stage(ServeState& st, const ReqDesc& dreq, uint64_t* seq_out) {
     ReqDesc d = dreq;
-    if (backlogged(st)) set_tile_units(d, std::max<uint32_t>(st.tile_chunks, kBacklogTileChunks));
+    if (backlogged(st)) {
+        set_tile_units(d, std::max<uint32_t>(st.tile_chunks, kBacklogTileChunks));
+    } else if (d.mode == KGPU_MODE_CBC_ENC && !(d.flags & (kDescSrcHost | kDescDstHost))) {
+        // a CBC-encryption request's latency is its chain time: while the ring
+        // keeps up, four lanes share each page's chain (8 pages a warp)
+        d.flags |= kDescQuad;
+        d.tile_units = kQuadPages;
+    }
     const uint64_t len = d.nblocks * 16;
     const uint64_t units = request_units(d);
     const uint64_t nt = (units + d.tile_units - 1) / d.tile_units;

@@ -223,6 +223,63 @@ __device__ __forceinline__ void tile_cbc_enc(const ReqDesc& d, uint64_t p0, uint
     }
 }
 
+// CBC encryption of pages [p0, p1) (at most kQuadPages), four lanes per page:
+// lane 4q + c holds column c of page q's chain state, so one chain advances
+// about twice as fast as with a lane per page, for a quarter of the pages per
+// warp -- the form for a lightly loaded device, where a request's latency is
+// its chain time.  Each round a lane fetches the three other columns of its
+// state from its quad (three independent shuffles), looks up its own column
+// (the two-table round of uni_col) and reads its own round-key word from the
+// warp's key slot (the quad's four words share one wavefront).  Lanes without
+// a page step along with predicated-off memory accesses.
+__device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
+    __syncwarp();
+    const uint32_t lane = lane_id();
+    const uint32_t c = lane & 3u, base = lane & ~3u;
+    const UniLanes L = uni_lanes(lane, 0);
+    const uint64_t page = p0 + (lane >> 2);
+    const bool valid = page < p1;
+    const uint32_t bpp = d.unit_blocks;
+    const uint32_t* in = reinterpret_cast<const uint32_t*>(d.src + (valid ? page : p0) * bpp) + c;
+    uint32_t* out = reinterpret_cast<uint32_t*>(d.dst + (valid ? page : p0) * bpp) + c;
+    const uint32_t key = K.data_saddr + 4u * c;  // word 4r + c of the schedule: round r, this column
+    auto key_word = [&](int r) {
+        uint32_t v;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(key + 16u * (uint32_t)r));
+        return v;
+    };
+    const uint32_t s1 = base | ((c + 1) & 3u), s2 = base | ((c + 2) & 3u), s3 = base | ((c + 3) & 3u);
+    uint32_t x = valid ? reinterpret_cast<const uint32_t*>(d.ivs + page)[c] : 0u;
+    // the chain is sequential, so plaintext is fetched four blocks ahead
+    uint32_t q0 = valid ? in[0] : 0u;
+    uint32_t q1 = valid && bpp > 1 ? in[4] : 0u;
+    uint32_t q2 = valid && bpp > 2 ? in[8] : 0u;
+    uint32_t q3 = valid && bpp > 3 ? in[12] : 0u;
+    const int nr = K.nr;
+    for (uint32_t i = 0; i < bpp; ++i) {
+        const uint32_t cur = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        if (valid && i + 4 < bpp) q3 = in[4 * (i + 4)];
+        x ^= cur ^ key_word(0);
+#pragma unroll 1
+        for (int r = 1; r < nr; r++) {
+            const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
+            const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
+            const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
+            x = uni_col(x, a1, a2, a3, key_word(r), L);
+        }
+        const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
+        const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
+        const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
+#define KGPU_FIN(P, v) lds_tab<kSmemBase>(row_addr<P>(v, L.f))
+        x = merge_bytes(KGPU_FIN(0, x), KGPU_FIN(1, a1), KGPU_FIN(2, a2), KGPU_FIN(3, a3)) ^ key_word(14);
+#undef KGPU_FIN
+        if (valid) out[4 * i] = x;
+    }
+}
+
 // CBC encryption of pages in registered host memory.  Over the host link a
 // load moves a whole 128-byte line, so the one-lane-per-page accesses above
 // would carry 16 useful bytes of every 128.  Here the warp moves 8 blocks
@@ -295,7 +352,10 @@ __device__ __forceinline__ uint32_t find_request(const uint64_t* tile_start, uin
 }
 
 // Runs one tile of request d; returns 0 or a KGPU_E* status for the request.
-// stage: this warp's scratch area, or null.
+// stage: this warp's scratch area, or null.  QUAD: compile the four-lanes-per-
+// page CBC encryption in (only the serving kernel's descriptors ask for it,
+// and it would cost the batch kernels registers).
+template <bool QUAD>
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
                                      WarpKeys& K, uint32_t& cur_sel, uint4* stage) {
     const uint32_t lane = lane_id();
@@ -328,8 +388,10 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
         case KGPU_MODE_ECB: tile_blocks<false>(d, u0, u1, dir, K); break;
         case KGPU_MODE_CBC_DEC: tile_cbc_dec(d, u0, u1, K); break;
         case KGPU_MODE_CBC_ENC:
-            if (stage && d.host && d.unit_blocks % kStageBlocks == 0)
+            if (stage && (d.flags & (kDescSrcHost | kDescDstHost)) && d.unit_blocks % kStageBlocks == 0)
                 tile_cbc_enc_staged(d, u0, u1, K, stage);
+            else if (QUAD && (d.flags & kDescQuad))
+                tile_cbc_enc_quad(d, u0, u1, K);
             else
                 tile_cbc_enc(d, u0, u1, K);
             break;
@@ -408,7 +470,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
         const uint32_t k = find_request(tile_start, nreq, t);
         const uint32_t i = order[k];
         const ReqDesc d = reqs[i];
-        const int st = run_tile(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile<false>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
         if (st && lane == 0) a.status[i] = st;
         if (a.fin) {
             // per-request completion: the warp that finishes a request's last
@@ -631,7 +693,7 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         const unsigned long long seq = a.dslots[s].seq;
         const unsigned long long t_first = __shfl_sync(0xffffffffu, gtimer(), 0);
         if (k == 0) a.t_start[s] = t_first;  // same value from every lane
-        const int st = run_tile(d, k, a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile<true>(d, k, a.keys, a.max_keys, K, cur_sel, stage);
         if (st) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
         // Publication: the warp barrier orders every lane's stores before
         // lane 0, lane 0's acq_rel increment releases them at GPU scope, the

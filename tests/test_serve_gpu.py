@@ -344,3 +344,51 @@ def test_serve_stamps_survive_slot_reuse(ctx):
         assert np.array_equal(t.got(i, 0), t.expected(i)), i
         assert np.array_equal(t.got(i, 1), t.expected(i)), i
     t.close()
+
+
+@pytest.mark.parametrize("bits", [128, 192, 256])
+def test_serve_cbc_encrypt_four_lanes_per_page(ctx, bits):
+    """While the ring keeps up, CBC encryption of device pages runs four lanes
+    to a page (tiles of 8 pages).  Requests published one at a time (never a
+    backlog) with pages of 1, 3, 256 and 257 blocks and 1 to 19 pages -- one
+    tile, several, ragged last tiles -- and in place: every output equals the
+    oracle."""
+    import torch
+    import paper_1305_3345_gb300 as kg
+    key = w.single_key(81 + bits, bits)
+    kh = ctx.setkey(key, False)
+    cases = [(bpp * 16, npg) for bpp in (1, 3, 256, 257) for npg in (1, 7, 8, 9, 19)]
+    total = sum(p * n for p, n in cases)
+    data = w.seeded_bytes(81, w.STREAM_DATA, total)
+    ivs_np = w.page_ivs(81, sum(n for _, n in cases))
+    src = torch.from_numpy(data.copy()).cuda()
+    dst = torch.zeros_like(src)
+    ivs = torch.from_numpy(ivs_np.reshape(-1).copy()).cuda()
+    torch.cuda.synchronize()
+    reqs, off, ivo = [], 0, 0
+    for i, (page, npg) in enumerate(cases):
+        r = np.zeros(1, dtype=kg.request_dtype())[0]
+        r["mode"], r["key"], r["len"], r["unit_size"] = w.MODE_CBC_ENC, kh, page * npg, page
+        inplace = i % 4 == 3
+        r["src"] = (dst if inplace else src).data_ptr() + off
+        r["dst"] = dst.data_ptr() + off
+        r["ivs"] = ivs.data_ptr() + 16 * ivo
+        reqs.append((r, off, page, npg, ivo, inplace))
+        off += page * npg
+        ivo += npg
+    for r, o, page, npg, io, inplace in reqs:   # in-place requests read their own region of dst
+        if inplace:
+            dst[o:o + page * npg].copy_(src[o:o + page * npg])
+    torch.cuda.synchronize()
+    ctx.serve_start()
+    try:
+        for r, *_ in reqs:
+            rc, st, _ = ctx.serve_poll(ctx.serve_submit(r), 10_000_000_000)
+            assert rc == 0 and st == 0
+    finally:
+        assert ctx.serve_stop(5_000_000_000) == 0
+    got = dst.cpu().numpy()
+    for r, o, page, npg, io, inplace in reqs:
+        ref = oracle.cbc(key, 0, data[o:o + page * npg], page, ivs_np[io:io + npg])
+        assert np.array_equal(got[o:o + page * npg], ref), (page, npg, inplace)
+    ctx.delkey(kh)
