@@ -232,8 +232,8 @@ __device__ __forceinline__ void tile_cbc_enc(const ReqDesc& d, uint64_t p0, uint
 // (the two-table round of uni_col) and reads its own round-key word from the
 // warp's key slot (the quad's four words share one wavefront).  Lanes without
 // a page step along with predicated-off memory accesses.
-__device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
-    __syncwarp();
+template <int NR>
+__device__ __forceinline__ void quad_chains(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
     const uint32_t lane = lane_id();
     const uint32_t c = lane & 3u, base = lane & ~3u;
     const UniLanes L = uni_lanes(lane, 0);
@@ -255,7 +255,6 @@ __device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0,
     uint32_t q1 = valid && bpp > 1 ? in[4] : 0u;
     uint32_t q2 = valid && bpp > 2 ? in[8] : 0u;
     uint32_t q3 = valid && bpp > 3 ? in[12] : 0u;
-    const int nr = K.nr;
     for (uint32_t i = 0; i < bpp; ++i) {
         const uint32_t cur = q0;
         q0 = q1;
@@ -263,8 +262,8 @@ __device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0,
         q2 = q3;
         if (valid && i + 4 < bpp) q3 = in[4 * (i + 4)];
         x ^= cur ^ key_word(0);
-#pragma unroll 1
-        for (int r = 1; r < nr; r++) {
+#pragma unroll
+        for (int r = 1; r < NR; r++) {
             const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
             const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
             const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
@@ -277,6 +276,17 @@ __device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0,
         x = merge_bytes(KGPU_FIN(0, x), KGPU_FIN(1, a1), KGPU_FIN(2, a2), KGPU_FIN(3, a3)) ^ key_word(14);
 #undef KGPU_FIN
         if (valid) out[4 * i] = x;
+    }
+}
+
+// The rounds are unrolled per key size: a lone chain is latency-bound, and a
+// loop's branch would sit on its critical path every round.
+__device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
+    __syncwarp();
+    switch (K.nr) {
+        case 10: quad_chains<10>(d, p0, p1, K); break;
+        case 12: quad_chains<12>(d, p0, p1, K); break;
+        default: quad_chains<14>(d, p0, p1, K); break;
     }
 }
 
