@@ -275,7 +275,10 @@ typedef struct kgpu_tuning {
  * The descriptors are copied into one of four rotating pinned staging slots
  * (the paper's four static pinned buffers, section 3.2) and the submission is
  * replayed as a CUDA graph {copy in, clear, kernel, copy status out}.  When
- * all four slots hold unfinished batches, submit blocks until the oldest ends.
+ * all four slots hold unfinished batches, submit blocks until the oldest ends;
+ * when the slot it would reuse is being waited on by a kgpu_poll or
+ * kgpu_poll_each call, it returns KGPU_EBUSY (retry).  Reusing a slot does not
+ * end its batch's ticket (see kgpu_poll).
  * *out receives a ticket for kgpu_poll.  n == 0 gives a ticket that is
  * already complete.  Requests of one batch run concurrently and in no fixed
  * order: no request may write bytes that another request of the same batch
@@ -290,8 +293,11 @@ int kgpu_submit(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream s
  * that long.  Returns KGPU_OK when the batch is complete (req_status, if not
  * NULL, receives each request's status: 0, or KGPU_ENOENT if its key was
  * deleted before it ran), KGPU_ETIMEDOUT if it is still running, and
- * KGPU_ENOENT for an unknown ticket or one whose slot has since been reused
- * by a later submission.
+ * KGPU_ENOENT for a ticket never issued.  A ticket whose slot a later
+ * submission has reused was complete by then (the submission waited for it):
+ * its poll returns KGPU_OK and its statuses from a record the library keeps
+ * of the newest 4096 such batches; older ones give KGPU_ENOENT.  Safe to call
+ * from several threads; while a call waits, its slot is not reused.
  */
 int kgpu_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *req_status);
 
@@ -307,8 +313,10 @@ int kgpu_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *req_st
  * timeout_ns < 0: no limit; otherwise KGPU_ETIMEDOUT after that long with
  * some requests still running (done_ns[i] = 0 for those).  While a call waits
  * on a ticket, a kgpu_submit that would reuse its staging slot returns
- * KGPU_EBUSY instead.  Errors: KGPU_EINVAL, KGPU_ENOENT (unknown or retired
- * ticket), KGPU_EIO.
+ * KGPU_EBUSY instead.  A ticket whose slot had already been reused is
+ * complete: KGPU_OK, with done_ns[i] = 0 for every request (the times were
+ * not kept) and the statuses as kgpu_poll gives them.  Errors: KGPU_EINVAL,
+ * KGPU_ENOENT (as kgpu_poll), KGPU_EIO.
  */
 int kgpu_poll_each(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *req_status, uint64_t *done_ns);
 

@@ -84,6 +84,26 @@ void free_slot(kgpu::BatchSlot& s) {
     s.gen = gen;
 }
 
+// Keep what polls of the slot's finished batch report once the slot is
+// reused: its request count and the failed requests' codes.  Caller holds
+// batch_mu; the batch has completed.
+void retire(kgpu_ctx* ctx, const kgpu::BatchSlot& s) {
+    kgpu::RetiredBatch r;
+    r.n = s.nreq;
+    for (uint32_t i = 0; i < s.nreq; i++)
+        if (s.h_status[i]) r.failed.emplace_back(i, s.h_status[i]);
+    ctx->retired[s.gen] = std::move(r);
+    while (ctx->retired.size() > kgpu::kRetiredKept) ctx->retired.erase(ctx->retired.begin());
+}
+
+int retired_status(const kgpu::RetiredBatch& r, int* req_status) {
+    if (req_status) {
+        std::memset(req_status, 0, r.n * sizeof(int));
+        for (const auto& f : r.failed) req_status[f.first] = f.second;
+    }
+    return KGPU_OK;
+}
+
 // Whether a batch holds CBC encryption of registered host pages (run through
 // the per-warp staging of the 512-thread batch kernel).
 bool needs_staging(const kgpu_request* reqs, size_t n) {
@@ -288,16 +308,19 @@ int kgpu_submit(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kgpu_stream s
     if (t.threads > 512 && needs_staging(reqs, n)) t.threads = 512;
     const uint64_t ticket = ++ctx->next_ticket;
     kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
-    // a batch someone waits on with kgpu_poll_each keeps its slot
+    // a batch someone waits on (kgpu_poll, kgpu_poll_each) keeps its slot
     if (s.pollers > 0) {
         --ctx->next_ticket;
         return KGPU_EBUSY;
     }
     // rotate: the slot's previous batch must have finished before its
-    // staging buffers are refilled
-    if (s.issued && cudaEventSynchronize(s.done) != cudaSuccess) {
-        cudaGetLastError();
-        return KGPU_EIO;
+    // staging buffers are refilled; its polls keep working from the record
+    if (s.issued) {
+        if (cudaEventSynchronize(s.done) != cudaSuccess) {
+            cudaGetLastError();
+            return KGPU_EIO;
+        }
+        retire(ctx, s);
     }
     s.issued = false;
     int rc = prepare_slot(ctx, s, n ? n : 1, t);
@@ -327,7 +350,13 @@ int kgpu_poll_each(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* r
     {
         std::lock_guard<std::mutex> lk(ctx->batch_mu);
         kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
-        if (ticket == 0 || s.gen != ticket || !s.issued) return KGPU_ENOENT;
+        if (ticket == 0 || ticket > ctx->next_ticket) return KGPU_ENOENT;
+        if (s.gen != ticket || !s.issued) {  // complete, slot since reused: times unknown
+            auto it = ctx->retired.find(ticket);
+            if (it == ctx->retired.end()) return KGPU_ENOENT;
+            for (uint32_t i = 0; i < it->second.n; i++) done_ns[i] = 0;
+            return retired_status(it->second, req_status);
+        }
         words = s.h_done;
         n = s.nreq;
         tag = s.tag;
@@ -378,8 +407,13 @@ int kgpu_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* req_st
     {
         std::lock_guard<std::mutex> lk(ctx->batch_mu);
         kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
-        if (ticket == 0 || s.gen != ticket || !s.issued) return KGPU_ENOENT;
+        if (ticket == 0 || ticket > ctx->next_ticket) return KGPU_ENOENT;
+        if (s.gen != ticket || !s.issued) {  // complete, slot since reused
+            auto it = ctx->retired.find(ticket);
+            return it == ctx->retired.end() ? KGPU_ENOENT : retired_status(it->second, req_status);
+        }
         ev = s.done;
+        s.pollers++;  // the slot is not reused while this call waits on it
     }
     DeviceGuard g(ctx->device);
     cudaError_t e;
@@ -393,14 +427,14 @@ int kgpu_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* req_st
             std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
     }
+    std::lock_guard<std::mutex> lk(ctx->batch_mu);
+    kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
+    s.pollers--;
     if (e == cudaErrorNotReady) return KGPU_ETIMEDOUT;
     if (e != cudaSuccess) {
         cudaGetLastError();
         return KGPU_EIO;
     }
-    std::lock_guard<std::mutex> lk(ctx->batch_mu);
-    kgpu::BatchSlot& s = ctx->slots[ticket % kBatchSlots];
-    if (s.gen != ticket) return KGPU_ENOENT;
     if (req_status && s.nreq) std::memcpy(req_status, s.h_status, s.nreq * sizeof(int));
     return KGPU_OK;
 }

@@ -33,7 +33,7 @@ struct BatchSlot {
     unsigned long long* h_done = nullptr;  // pinned, mapped: per-request completion words
     unsigned long long* d_done = nullptr;  // the device's view of h_done
     uint32_t tag = 0;                      // completion tag of the slot's current batch
-    int pollers = 0;                       // kgpu_poll_each calls holding the slot
+    int pollers = 0;                       // kgpu_poll / kgpu_poll_each calls holding the slot
     unsigned long long* d_counter = nullptr;
     uint4* d_scratch = nullptr;  // per-warp staging for CBC encryption of host pages
     uint32_t scratch_warps = 0;
@@ -47,6 +47,14 @@ struct BatchSlot {
 };
 
 constexpr int kBatchSlots = 4;
+
+// A batch whose slot was reused by a later submission: it had completed (the
+// submission waited for it), and this is what its polls still report.
+struct RetiredBatch {
+    uint32_t n = 0;                                // requests
+    std::vector<std::pair<uint32_t, int>> failed;  // (request, KGPU_E* status) of the failed ones
+};
+constexpr size_t kRetiredKept = 4096;  // the newest retired batches are kept
 
 // Serving state (kgpu_serve_*): the mapped host ring, the device counters and
 // the host's bookkeeping of what is in flight.
@@ -120,6 +128,7 @@ struct kgpu_ctx {
     // batched submission (kgpu_submit / kgpu_poll)
     std::mutex batch_mu;
     kgpu::BatchSlot slots[kgpu::kBatchSlots];
+    std::map<uint64_t, kgpu::RetiredBatch> retired;  // by ticket; guarded by batch_mu
     uint64_t next_ticket = 0;
     kgpu_tuning tune{};
 

@@ -173,13 +173,18 @@ def test_ticket_rotation(ctx):
     import paper_1305_3345_gb300 as kg
     b = Batch(ctx, seed=61, n=20, lo=4096, hi=65536, nkeys=4)
     tickets = [ctx.submit(b.reqs) for _ in range(6)]
-    # the last four slots are still addressable, the first two were reused
+    # the last four hold the slots; the first two were complete when their
+    # slots were reused, and still poll as complete with every status 0
     assert ctx.poll(tickets[-1], -1) == 0
     for t in tickets[-4:]:
         assert ctx.poll(t, 0) == 0
     for t in tickets[:2]:
-        with pytest.raises(kg.KgpuError):
-            ctx.poll(t, 0)
+        st = np.full(len(b.reqs), 7, np.int32)
+        assert ctx.poll(t, 0, status=st) == 0 and not st.any()
+        rc, done = ctx.poll_each(t, len(b.reqs))
+        assert rc == 0 and not done.any()          # complete, times not kept
+    with pytest.raises(kg.KgpuError):
+        ctx.poll(tickets[-1] + 1000, 0)              # never issued
     for i in range(len(b.reqs)):
         assert np.array_equal(b.got(i), b.expected(i))
     b.close()
