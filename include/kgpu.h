@@ -412,7 +412,11 @@ int kgpu_serve_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *
 
 /* Wait (at most drain_timeout_ns; < 0: no limit) for every published request
  * to complete, stop the kernel and free the ring.  KGPU_ETIMEDOUT if requests
- * were still pending at the limit (the kernel is stopped all the same). */
+ * were still pending at the limit (the kernel is stopped all the same).  Safe
+ * against other threads: submissions made once a stop has begun are refused
+ * (KGPU_EINVAL); kgpu_serve_poll and kgpu_replay_serve calls still running
+ * when the ring is drained return KGPU_ENOENT within about 50 us, and the ring
+ * is freed only after they have; a second concurrent stop waits for the first. */
 int kgpu_serve_stop(kgpu_ctx *ctx, int64_t drain_timeout_ns);
 
 int kgpu_serve_get_stats(kgpu_ctx *ctx, kgpu_serve_stats *out);

@@ -60,6 +60,12 @@ constexpr size_t kRetiredKept = 4096;  // the newest retired batches are kept
 // the host's bookkeeping of what is in flight.
 struct ServeState {
     bool started = false;
+    // Calls reading the ring's mapped words outside serve_mu (kgpu_serve_poll,
+    // kgpu_replay_serve): kgpu_serve_stop frees the ring only once none is
+    // left, and after it sets `stopping` they return instead of waiting.
+    int readers = 0;
+    bool stopping = false;
+    bool closing = false;  // a kgpu_serve_stop is under way: further stops wait for it, submits are refused
     bool running = false;  // a kernel instance was launched and has not been seen to exit
     cudaStream_t stream = nullptr;
     cudaEvent_t kdone = nullptr;

@@ -239,6 +239,18 @@ bool read_completed(const ServeState& st, uint64_t seq, int* status, uint64_t* t
     return false;
 }
 
+// Leaves the readers count of a call that read the ring outside serve_mu.
+struct ReaderGuard {
+    kgpu_ctx* ctx;
+    explicit ReaderGuard(kgpu_ctx* c) : ctx(c) {}
+    ~ReaderGuard() {
+        std::lock_guard<std::mutex> lk(ctx->serve_mu);
+        ctx->serve.readers--;
+    }
+    ReaderGuard(const ReaderGuard&) = delete;
+    ReaderGuard& operator=(const ReaderGuard&) = delete;
+};
+
 // Publish a validated descriptor.  Caller holds serve_mu.
 // Tile size of requests staged while the ring is backed up (512-byte chunks).
 constexpr uint32_t kBacklogTileChunks = 64;  // 32 KiB
@@ -384,7 +396,7 @@ int kgpu_serve_submit(kgpu_ctx* ctx, const kgpu_request* req, kgpu_ticket* ticke
     RangeCache rc;
     std::lock_guard<std::mutex> lk(ctx->serve_mu);
     ServeState& st = ctx->serve;
-    if (!st.started) return KGPU_EINVAL;
+    if (!st.started || st.closing) return KGPU_EINVAL;
     int r = make_desc(ctx, *req, rc, st.tile_chunks, &d);
     if (r) return r;
     uint64_t seq = 0;
@@ -402,7 +414,7 @@ int kgpu_serve_submit_many(kgpu_ctx* ctx, const kgpu_request* reqs, size_t n, kg
     RangeCache rc;
     std::lock_guard<std::mutex> lk(ctx->serve_mu);
     ServeState& st = ctx->serve;
-    if (!st.started) return KGPU_EINVAL;
+    if (!st.started || st.closing) return KGPU_EINVAL;
     for (size_t i = 0; i < n; i++) {  // all or nothing on validation
         if (reqs[i].len == 0) return KGPU_EINVAL;
         int r = make_desc(ctx, reqs[i], rc, st.tile_chunks, &descs[i]);
@@ -428,8 +440,10 @@ int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* 
     ServeState& st = ctx->serve;
     {
         std::lock_guard<std::mutex> lk(ctx->serve_mu);
-        if (!st.started || ticket == 0 || ticket > st.next_seq) return KGPU_ENOENT;
+        if (!st.started || st.stopping || ticket == 0 || ticket > st.next_seq) return KGPU_ENOENT;
+        st.readers++;
     }
+    ReaderGuard reader(ctx);
     const uint64_t seq = ticket - 1;
     const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
     const uint64_t t0 = now_ns();
@@ -457,7 +471,7 @@ int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* 
         const uint64_t t = now_ns();
         if (timeout_ns == 0 || t - last_check > 50000) {
             std::lock_guard<std::mutex> lk(ctx->serve_mu);
-            if (!st.started) return KGPU_ENOENT;
+            if (!st.started || st.stopping) return KGPU_ENOENT;
             reap(st);
             if (!st.outstanding.empty()) {
                 int rc = ensure_running(ctx, st);
@@ -475,6 +489,15 @@ int kgpu_serve_stop(kgpu_ctx* ctx, int64_t drain_timeout_ns) {
     std::unique_lock<std::mutex> lk(ctx->serve_mu);
     ServeState& st = ctx->serve;
     if (!st.started) return KGPU_OK;
+    if (st.closing) {  // another thread is stopping this ring: wait until it is gone
+        while (st.started && st.closing) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+            lk.lock();
+        }
+        return KGPU_OK;
+    }
+    st.closing = true;
     const uint64_t t0 = now_ns();
     int rc = KGPU_OK;
     for (;;) {
@@ -497,6 +520,13 @@ int kgpu_serve_stop(kgpu_ctx* ctx, int64_t drain_timeout_ns) {
     if (cudaEventSynchronize(st.kdone) != cudaSuccess) {
         cudaGetLastError();
         if (!rc) rc = KGPU_EIO;
+    }
+    // calls still reading the ring see `stopping` within 50 us and leave
+    st.stopping = true;
+    while (st.readers > 0) {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
     }
     serve_free(st);
     return rc;
@@ -532,10 +562,12 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
     uint32_t nslots;
     {
         std::lock_guard<std::mutex> lk(ctx->serve_mu);
-        if (!ctx->serve.started) return KGPU_EINVAL;
+        if (!ctx->serve.started || ctx->serve.stopping) return KGPU_EINVAL;
         tile_chunks = ctx->serve.tile_chunks;
         nslots = ctx->serve.nslots;
+        ctx->serve.readers++;
     }
+    ReaderGuard reader(ctx);
     {
         RangeCache rc;
         for (size_t i = 0; i < n; i++) {
@@ -593,7 +625,8 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
                 // not queue behind it, or completions go unseen meanwhile.
                 std::unique_lock<std::mutex> lk(ctx->serve_mu, std::defer_lock);
                 if (produced.load(std::memory_order_acquire) < n ? lk.try_lock() : (lk.lock(), true)) {
-                    if (!pending.empty() && ensure_running(ctx, st)) error.store(KGPU_EIO);
+                    if (st.stopping) error.store(KGPU_ENOENT);
+                    else if (!pending.empty() && ensure_running(ctx, st)) error.store(KGPU_EIO);
                     last_check = t;
                 }
             }

@@ -392,3 +392,71 @@ def test_serve_cbc_encrypt_four_lanes_per_page(ctx, bits):
         ref = oracle.cbc(key, 0, data[o:o + page * npg], page, ivs_np[io:io + npg])
         assert np.array_equal(got[o:o + page * npg], ref), (page, npg, inplace)
     ctx.delkey(kh)
+
+
+def test_serve_stop_while_other_threads_poll(ctx):
+    """kgpu_serve_stop from one thread while others poll tickets (some of them
+    already complete, some never issued yet) and another thread keeps trying
+    to submit: the stop drains and frees the ring without a reader left on it,
+    every poll returns OK or ENOENT, submissions after the stop began are
+    refused, and a second stop in parallel returns once the first is done."""
+    import threading
+    import time
+    import paper_1305_3345_gb300 as kg
+    t = Traffic(ctx, seed=83, n=120, lo=4096, hi=256 << 10, nkeys=8)
+    ctx.serve_start()
+    tickets = [submit_retry(ctx, r) for r in t.reqs[:60]]
+    results, errors = [], []
+    stop_started = threading.Event()
+
+    def poller(ts):
+        try:
+            for tk in ts:
+                try:
+                    rc, st, _ = ctx.serve_poll(tk, 20_000_000_000)
+                    results.append((tk, rc, st))
+                except kg.KgpuError as e:
+                    results.append((tk, e.code, None))
+        except Exception as e:  # reported below
+            errors.append(repr(e))
+
+    def submitter():
+        refused = 0
+        for r in t.reqs[60:]:
+            try:
+                ctx.serve_submit(r)
+            except kg.KgpuError as e:
+                if e.code not in ("EBUSY", "EINVAL"):
+                    errors.append(repr(e))
+                refused += e.code == "EINVAL"
+            if stop_started.is_set() and refused:
+                return
+
+    def stopper(out):
+        stop_started.set()
+        out.append(ctx.serve_stop(30_000_000_000))
+
+    stops = []
+    ths = [threading.Thread(target=poller, args=(tickets[i::3],)) for i in range(3)]
+    ths += [threading.Thread(target=submitter)]
+    for th in ths:
+        th.start()
+    time.sleep(0.002)
+    s1 = threading.Thread(target=stopper, args=(stops,))
+    s2 = threading.Thread(target=stopper, args=(stops,))
+    s1.start()
+    s2.start()
+    for th in ths + [s1, s2]:
+        th.join(60)
+    assert not errors, errors
+    assert sorted(stops) == [0, 0]
+    assert all(rc in (0, "ENOENT") for _, rc, _ in results)
+    assert all(st == 0 for _, rc, st in results if rc == 0)
+    # the ring is gone: a poll of an old ticket is ENOENT, and serving restarts cleanly
+    with pytest.raises(kg.KgpuError):
+        ctx.serve_poll(tickets[0], 0)
+    ctx.serve_start()
+    tk = ctx.serve_submit(t.reqs[0])
+    assert ctx.serve_poll(tk, 10_000_000_000)[0] == 0
+    assert ctx.serve_stop(5_000_000_000) == 0
+    t.close()
