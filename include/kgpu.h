@@ -20,8 +20,10 @@
  *  - src and dst must be 16-byte aligned.  src == dst (in place) is allowed
  *    for every mode; any other overlap is KGPU_EINVAL.
  *  - Lengths are in bytes and must be whole data units / pages; the unit size
- *    must be a nonzero multiple of 16.  There is no padding and no ciphertext
- *    stealing.  len == 0 is a no-op.
+ *    must be a nonzero multiple of 16, except the XTS data unit of
+ *    kgpu_aes_xts_crypt, which may be any size from 16 bytes (a unit ending in
+ *    a partial block uses ciphertext stealing).  There is no padding.
+ *    len == 0 is a no-op.
  *  - Device work is asynchronous on the caller's stream (0 = legacy default
  *    stream).  A launch failure is reported as KGPU_EIO; an asynchronous fault
  *    surfaces from the next synchronising CUDA call on that stream.
