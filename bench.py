@@ -666,12 +666,12 @@ def run_kgpu(args):
     import paper_1305_3345_gb300 as kg
 
     rank, world, local = dist_env()
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)  # before the process group, so NCCL binds each rank to its own GPU
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = local if world > 1 else 0
-    torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
 
     ctx = kg.Context(dev)
