@@ -156,7 +156,7 @@ def recorded_traffic():
 
 
 ALU_LANE_OPS_PER_CLK_SM = 64  # LOP3 / PRMT / SHF issue rate of one SM, measured on the GB300
-BITSLICE_SOURCES = ("aes_device.cuh", "kgpu_bitslice.cu", "sbox_circuit.cuh", "kgpu_internal.h")
+BITSLICE_SOURCES = ("aes_device.cuh", "kgpu_bitslice.cu", "sbox_circuit.cuh", "kgpu_bitslice.h")
 
 
 def bitslice_hash() -> str:

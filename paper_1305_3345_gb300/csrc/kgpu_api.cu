@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "aes_tables_host.h"
+#include "kgpu_bitslice.h"
 #include "kgpu_ctx.h"
 
 using namespace kgpu;

@@ -26,7 +26,7 @@
 #include <cuda_runtime.h>
 
 #include "aes_device.cuh"
-#include "kgpu_internal.h"
+#include "kgpu_bitslice.h"
 #include "sbox_circuit.cuh"
 
 namespace kgpu {

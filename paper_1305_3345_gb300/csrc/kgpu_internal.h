@@ -177,22 +177,6 @@ constexpr int kMboxStride = 16;  // words between two CTAs' mailboxes (128 B)
 // Largest tile count of one served request (a request must fit the tile ring).
 inline uint64_t serve_max_tiles(uint64_t tile_ring) { return tile_ring / 2; }
 
-// Bitsliced kernels (kgpu_bitslice.cu): 32 blocks per thread as 128 bit-planes.
-constexpr int kBsThreads = 384;  // 168 registers: 12 warps per SM (see the kernel's comment)
-struct BsParams {
-    const uint4* src;
-    uint4* dst;
-    uint4* tw;              // XTS: one tweak E_K2(unit) per data unit of the call
-    uint64_t nblocks;       // 16-byte blocks (main kernel)
-    uint64_t units;         // data units (tweak pre-pass)
-    uint64_t first_sector;  // number of the first data unit
-    uint32_t bps;           // blocks per data unit
-    uint32_t pad;
-    uint32_t rkm[128 * 15]; // round-key plane masks (0 or ~0), (Nr + 1) x 128
-};
-cudaError_t launch_bitsliced(const BsParams& p, int nr, bool tweak, int num_sms, cudaStream_t s);
-cudaError_t launch_bitsliced_tweaks(const BsParams& p, int nr, int num_sms, cudaStream_t s);
-
 // Launch entry points of the unified kernels (kgpu_unified.cu).  They return
 // a cudaError_t from the launch.
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s);
