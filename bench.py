@@ -258,6 +258,49 @@ def pct(lat_ns):
     return {"p50_us": q(50), "p99_us": q(99), "p99.9_us": q(99.9), "max_us": float(a[-1])}
 
 
+def compact(obj, sig=5):
+    """obj with every float rounded to `sig` significant digits (the headline
+    line stays short)."""
+    if isinstance(obj, float):
+        return float(f"{obj:.{sig}g}")
+    if isinstance(obj, dict):
+        return {k: compact(v, sig) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [compact(v, sig) for v in obj]
+    return obj
+
+
+def _r(x, nd=1):
+    return None if x is None else round(float(x), nd)
+
+
+def batched_summary(b):
+    """A few numbers of the batched comparison for the headline line."""
+    bl, pl = b["batched"]["latency"] or {}, b["per_request"]["latency"] or {}
+    return {"requests": int(b["workload"].split()[0]),
+            "batched": {"GB/s": _r(b["batched"]["GB/s"]), "p50_ms": _r(bl.get("p50_us", 0) / 1e3, 2),
+                        "p99_ms": _r(bl.get("p99_us", 0) / 1e3, 2)},
+            "per_request": {"GB/s": _r(b["per_request"]["GB/s"]), "p50_ms": _r(pl.get("p50_us", 0) / 1e3, 2),
+                            "p99_ms": _r(pl.get("p99_us", 0) / 1e3, 2)}}
+
+
+def serving_summary(sv, svh, rt):
+    """p99 (us) of the serving ring and of one launch per request at each
+    offered rate, both residencies, plus the one-at-a-time 4 KiB round trip."""
+    def p99(d):
+        return _r((d.get("latency") or {}).get("p99_us"))
+    out = {"rates_req_s": [r["rate_req_s"] for r in sv["rates"]],
+           "device_ring_p99_us": [p99(r["ring"]) for r in sv["rates"]],
+           "device_per_request_p99_us": [p99(r["per_request"]) for r in sv["rates"]],
+           "host_ring_p99_us": [p99(r["ring"]) for r in svh["rates"]],
+           "host_per_request_p99_us": [p99(r["per_request"]) for r in svh["rates"]]}
+    if sv.get("ring_capacity"):
+        out["ring_capacity_GB/s"] = _r(sv["ring_capacity"]["ring"]["GB/s"])
+    out["roundtrip_4k_p50_p99_us"] = {k: [_r((rt[k]["latency"] or {}).get("p50_us")), p99(rt[k])]
+                                      for k in ("ring", "launch", "host_ring", "host_launch")}
+    return out
+
+
 def register_mix_keys(ctx, seed, mix):
     keys = w.mix_key_material(seed, mix)
     hx = np.array([ctx.setkey(k[: 2 * b // 8], True) for k, b in zip(keys, mix.key_bits)], dtype=np.uint32)
@@ -745,8 +788,7 @@ def run_kgpu(args):
     traffic = recorded_traffic()
     roofline = {"bound": "smem", "achieved": achieved_smem, "peak": smem_peak, "unit": "GB/s",
                 "frac": achieved_smem / smem_peak, "traffic": traffic,
-                "peak_source": f"{props.multi_processor_count} SMs x 128 B/clk x {sm_mhz:.0f} MHz "
-                               "(median SM clock sampled during the timed region)",
+                "peak_source": f"{props.multi_processor_count} SMs x 128 B/clk x {sm_mhz:.0f} MHz",
                 "kernel": "bulk_kernel<14,enc,xts>", "launch_ms": launch_s * 1e3}
     if bitsliced:
         # ALU-bound: lane-operations of the ALU pipe per block (counted once with
@@ -767,7 +809,13 @@ def run_kgpu(args):
                     "kernel": "bs_kernel<14,xts> (+ bs_tweak_kernel)", "launch_ms": launch_s * 1e3}
     roofline_hbm = {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_hbm / hbm_peak, "traffic": traffic,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s"}
+                    "peak_source": "measured hbm_gbs" if peaks else "fallback 6.8 TB/s"}
+
+    def emit(section, obj):
+        # secondary measurements go on lines of their own, before the headline
+        # (no "metric" key): the headline stays the last, short line
+        if rank == 0:
+            print(json.dumps({"section": section, **obj}), flush=True)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -813,7 +861,7 @@ def run_kgpu(args):
                 bound = smem_bound_clk / (lookups[name] * 4) * 16 / 1e9
                 extra[name]["smem_bound_GB/s"] = bound
                 extra[name]["frac_of_smem_bound"] = GIB / t / 1e9 / bound
-        line["extra"] = extra
+        emit("extra", {"modes": extra})
         ctx.delkey(k128)
         ctx.delkey(ck)
         del ivs
@@ -864,13 +912,11 @@ def run_kgpu(args):
             ctx.host_unregister(hsrc)
             ctx.host_unregister(hdst)
         line["e2e"] = {"value": world * GIB / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": world * GIB,
-                       "d2h_bytes_per_step": world * GIB, "steps": e2e_steps,
-                       "statistic": "median step", "mean_GB/s": world * GIB / dmean / 1e9,
-                       "call": "kgpu_aes_xts_crypt_host on pinned host pages registered once with "
-                               "kgpu_host_register: the kernel reads and writes them over the host link",
-                       "bytes_over_link": "h2d/d2h bytes are the kernel's own reads and writes of host memory"}
+                       "d2h_bytes_per_step": world * GIB, "steps": e2e_steps, "statistic": "median step",
+                       "call": "kgpu_aes_xts_crypt_host, registered pinned pages"}
         dt, dmean = host_steps()
-        line["e2e_copy_pipeline"] = {"value": world * GIB / dt / 1e9, "unit": "GB/s",
+        e2e_forms = {}
+        e2e_forms["e2e_copy_pipeline"] = {"value": world * GIB / dt / 1e9, "unit": "GB/s",
                                      "h2d_bytes_per_step": world * GIB, "d2h_bytes_per_step": world * GIB,
                                      "steps": e2e_steps, "chunk_bytes": chunk, "statistic": "median step",
                                      "mean_GB/s": world * GIB / dmean / 1e9,
@@ -898,23 +944,30 @@ def run_kgpu(args):
             dz = float(t.item())
         ctx.host_unregister(hsrc)
         ctx.host_unregister(hdst)
-        line["e2e_zero_copy"] = {"value": world * GIB / dz / 1e9, "unit": "GB/s",
+        e2e_forms["e2e_zero_copy"] = {"value": world * GIB / dz / 1e9, "unit": "GB/s",
                                  "link_bytes_per_step": {"host_to_device": world * GIB, "device_to_host": world * GIB},
                                  "steps": e2e_steps, "statistic": "median step",
                                  "call": "kgpu_submit + kgpu_poll, src/dst flagged host"}
+        emit("e2e_forms", e2e_forms)
         del hsrc, hdst
 
     if rank == 0 and not args.no_batched and (nbytes == GIB or args.batch_requests != 10000):
-        line["batched"] = run_batched(ctx, kg, dev, args.batch_requests)
+        b = run_batched(ctx, kg, dev, args.batch_requests)
+        emit("batched", b)
+        line["batched"] = batched_summary(b)
 
     if rank == 0 and not args.no_serve and nbytes == GIB:
-        line["serving"] = run_serving(ctx, kg, dev, args.serve_seconds)
-        line["serving_host"] = run_serving(ctx, kg, dev, args.serve_seconds, host=True)
-        line["roundtrip"] = run_roundtrip(ctx, kg, dev)
-        line["ecb_size_sweep"] = run_ecb_sweep(ctx, kg, dev)
+        sv = run_serving(ctx, kg, dev, args.serve_seconds)
+        emit("serving", sv)
+        svh = run_serving(ctx, kg, dev, args.serve_seconds, host=True)
+        emit("serving_host", svh)
+        rt = run_roundtrip(ctx, kg, dev)
+        emit("roundtrip", rt)
+        line["serving"] = serving_summary(sv, svh, rt)
+        emit("ecb_size_sweep", run_ecb_sweep(ctx, kg, dev))
 
     if rank == 0 and not args.no_host and nbytes == GIB:
-        line["host_stream"] = run_host_stream(ctx, kg, kh, dev)
+        emit("host_stream", run_host_stream(ctx, kg, kh, dev))
 
     if rank == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate()
@@ -922,7 +975,7 @@ def run_kgpu(args):
     ctx.delkey(kh)
     ctx.close()
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(compact(line), separators=(",", ":")), flush=True)
     if dist:
         dist.destroy_process_group()
 
