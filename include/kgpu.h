@@ -111,7 +111,12 @@ int kgpu_destroy(kgpu_ctx *ctx);
  */
 int kgpu_aes_setkey(kgpu_ctx *ctx, const uint8_t *key, size_t key_len, int xts, kgpu_key *out);
 
-/* Forget a key.  Work already submitted with it completes first. */
+/*
+ * Forget a key.  Work already submitted with it completes first: batches of
+ * kgpu_submit and kgpu_submit_noalloc, and requests published to the serving
+ * ring.  (Per-call transforms carry their key schedule in the launch.)  The
+ * handle may be reused by a later kgpu_aes_setkey.
+ */
 int kgpu_aes_delkey(kgpu_ctx *ctx, kgpu_key key);
 
 /*
@@ -449,7 +454,8 @@ int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t
  * ---------------------------------------------------------------------- */
 
 #define KGPU_NOALLOC_MAX_REQUESTS 512
-#define KGPU_NOALLOC_SCRATCH_BYTES 45056
+#define KGPU_NOALLOC_STAGE_WARPS 16
+#define KGPU_NOALLOC_SCRATCH_BYTES 110592
 
 /*
  * kgpu_submit for callers that cannot allocate memory when they call: for
@@ -458,23 +464,31 @@ int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t
  * allocation could block on the very reclaim it serves, or a deployment whose
  * memory budget is fixed at start-up.  It runs the same persistent batch
  * kernel, but its scratch (work counter, per-request status words, device copy
- * of the descriptors) is one fixed array of KGPU_NOALLOC_SCRATCH_BYTES of
- * device memory inside the library image, which every GPU that loads the
- * library holds until the process exits; the descriptors are packed in a fixed
- * host array.  The call makes no cudaMalloc/cudaFree or other allocating call.
+ * of the descriptors, and KGPU_NOALLOC_STAGE_WARPS warps' 4-KiB staging areas
+ * for CBC encryption of registered host pages) is one fixed array of
+ * KGPU_NOALLOC_SCRATCH_BYTES of device memory inside the library image, which
+ * every GPU that loads the library holds until the process exits; the
+ * descriptors are packed in a fixed host array.  The call makes no
+ * cudaMalloc/cudaFree or other allocating call.
  *
  * Arguments as kgpu_submit, without a ticket: the work is queued on `stream`
  * and the caller synchronises on that stream.  At most
  * KGPU_NOALLOC_MAX_REQUESTS requests per call: more is KGPU_E2BIG, with
  * nothing launched.  Validation as kgpu_submit (req_status, if not NULL,
- * receives each request's validation code); a key deleted while the batch runs
- * is not reported back.  The counter and status words are cleared on every
- * call, but every call shares the one array: calls whose work overlaps on the
- * GPU (on different streams, or from different threads without ordering)
- * race and corrupt each other -- order them on one stream or synchronise in
- * between.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.
+ * receives each request's validation code).  kgpu_aes_delkey and
+ * kgpu_host_unregister wait for batches queued here before they remove a key
+ * or a range, as they do for kgpu_submit.  A batch holding CBC encryption of
+ * host pages runs the 512-thread kernel, whose first
+ * KGPU_NOALLOC_STAGE_WARPS warps stage those pages; the other warps run them
+ * one lane per page (the same bytes, more link transfers).  The counter and
+ * status words are cleared on every call, but every call shares the one
+ * array: calls whose work overlaps on the GPU (on different streams, or from
+ * different threads without ordering) race and corrupt each other -- order
+ * them on one stream or synchronise in between.  A stream that is being
+ * captured into a CUDA graph is refused (KGPU_EINVAL): the descriptors are
+ * copied from a host array that the next call overwrites.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current).
  */
 int kgpu_submit_noalloc(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream stream, int *req_status);
 

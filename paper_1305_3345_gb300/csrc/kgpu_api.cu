@@ -77,6 +77,7 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
     if (rc == KGPU_OK) rc = from_cuda(cudaMalloc(&ctx->d_keys, sizeof(DevKey) * ctx->cfg.max_keys));
     if (rc == KGPU_OK) rc = from_cuda(cudaMemset(ctx->d_keys, 0, sizeof(DevKey) * ctx->cfg.max_keys));
     if (rc == KGPU_OK) rc = from_cuda(cudaStreamCreateWithFlags(&ctx->key_stream, cudaStreamNonBlocking));
+    if (rc == KGPU_OK) rc = from_cuda(cudaEventCreateWithFlags(&ctx->noalloc_done, cudaEventDisableTiming));
     if (rc != KGPU_OK) {
         cudaGetLastError();
         kgpu_destroy(ctx);
@@ -100,6 +101,10 @@ int kgpu_destroy(kgpu_ctx* ctx) {
             if (ctx->staging[i]) cudaFree(ctx->staging[i]);
         }
         destroy_batch_slots(ctx);
+        if (ctx->noalloc_done) {
+            cudaEventSynchronize(ctx->noalloc_done);
+            cudaEventDestroy(ctx->noalloc_done);
+        }
         if (ctx->key_stream) cudaStreamDestroy(ctx->key_stream);
         if (ctx->d_keys) cudaFree(ctx->d_keys);
         for (const HostRange& r : ctx->hreg)

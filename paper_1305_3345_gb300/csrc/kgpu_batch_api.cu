@@ -104,15 +104,6 @@ int retired_status(const kgpu::RetiredBatch& r, int* req_status) {
     return KGPU_OK;
 }
 
-// Whether a batch holds CBC encryption of registered host pages (run through
-// the per-warp staging of the 512-thread batch kernel).
-bool needs_staging(const kgpu_request* reqs, size_t n) {
-    for (size_t i = 0; i < n; i++)
-        if (reqs[i].mode == KGPU_MODE_CBC_ENC && (reqs[i].flags & (KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST)))
-            return true;
-    return false;
-}
-
 // Grow the slot's buffers to hold n requests and (re)build its graph when the
 // buffers or the launch shape changed.
 int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning& t) {
@@ -269,6 +260,12 @@ int batches_quiesce(kgpu_ctx* ctx) {
             cudaGetLastError();
             return KGPU_EIO;
         }
+    }
+    // allocation-free batches: every one issued before this call is ordered
+    // before the newest on its stream, or was synchronised by its caller
+    if (ctx->noalloc_issued && cudaEventSynchronize(ctx->noalloc_done) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
     }
     return KGPU_OK;
 }

@@ -137,6 +137,10 @@ struct kgpu_ctx {
     std::map<uint64_t, kgpu::RetiredBatch> retired;  // by ticket; guarded by batch_mu
     uint64_t next_ticket = 0;
     kgpu_tuning tune{};
+    // the newest kgpu_submit_noalloc batch: recorded on the caller's stream
+    // after its launch (guarded by batch_mu), waited on by batches_quiesce
+    cudaEvent_t noalloc_done = nullptr;
+    bool noalloc_issued = false;
 
     // serving loop (kgpu_serve_*)
     std::mutex serve_mu;
@@ -345,6 +349,15 @@ inline void set_tile_units(ReqDesc& d, uint32_t tile_chunks) {
 // chunks for XTS/ECB; CBC tiles derive from it).  Cache: anything with
 // int check(const kgpu_ctx*, const void*, size_t) -- RangeCache, or a
 // fixed-capacity cache where the caller must not allocate.
+// Whether a batch holds CBC encryption of registered host pages (run through
+// the per-warp staging of the 512-thread batch kernel).
+inline bool needs_staging(const kgpu_request* reqs, size_t n) {
+    for (size_t i = 0; i < n; i++)
+        if (reqs[i].mode == KGPU_MODE_CBC_ENC && (reqs[i].flags & (KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST)))
+            return true;
+    return false;
+}
+
 template <class Cache>
 int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chunks, ReqDesc* d) {
     std::memset(d, 0, sizeof(*d));

@@ -23,11 +23,18 @@ using namespace kgpu::hostutil;
 
 namespace {
 
+// Layout of the fixed scratch: the work counter, the per-request status
+// words, the device copy of the packed batch, then the staging areas of
+// kStageWarps warps for CBC encryption of registered host pages.
 constexpr size_t kCounterOff = 0;
 constexpr size_t kStatusOff = 256;
 constexpr size_t kBatchOff = kStatusOff + ((KGPU_NOALLOC_MAX_REQUESTS * sizeof(int) + 255) / 256) * 256;
-static_assert(kBatchOff + batch_bytes(KGPU_NOALLOC_MAX_REQUESTS) <= KGPU_NOALLOC_SCRATCH_BYTES,
+constexpr size_t kStageOff = 45056;
+constexpr uint32_t kStageWarps = KGPU_NOALLOC_STAGE_WARPS;
+static_assert(kBatchOff + batch_bytes(KGPU_NOALLOC_MAX_REQUESTS) <= kStageOff,
               "the fixed scratch must hold the largest batch");
+static_assert(kStageOff % 256 == 0 && kStageOff + kStageWarps * kStageWarpBytes <= KGPU_NOALLOC_SCRATCH_BYTES,
+              "the fixed scratch must hold the staging areas");
 
 // The scratch.  In host code this name is only a host-side stand-in for the
 // symbol, never a device address: the device address comes from
@@ -38,8 +45,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_dev[kMaxDevices] = {};
 
-// Host staging for the packed batch (pageable; cudaMemcpyAsync has copied it
-// out by the time it returns, so one array serves every call in turn).
+// Host staging for the packed batch, in pageable memory.  This relies on the
+// CUDA runtime's documented behaviour for an asynchronous copy from pageable
+// host memory to device memory: the call returns once the source has been
+// copied into the runtime's own staging memory, and only the DMA to the
+// device may still be pending.  Under that assumption the array can be
+// refilled as soon as the copy call returns, so one array serves every call in
+// turn under g_pack_mu.  (A stream being captured into a graph breaks the
+// assumption -- the graph would keep this address -- so such calls are
+// refused.)
 std::mutex g_pack_mu;
 alignas(256) unsigned char g_pack[batch_bytes(KGPU_NOALLOC_MAX_REQUESTS)];
 
@@ -89,18 +103,27 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
     if (n > KGPU_NOALLOC_MAX_REQUESTS) return KGPU_E2BIG;
     if (n == 0) return KGPU_OK;
     DeviceGuard g(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        // a capturing stream (or, for the legacy stream, a capture elsewhere)
+        cudaGetLastError();
+        return KGPU_EINVAL;
+    }
     unsigned char* scratch = nullptr;
     int rc = scratch_on(ctx, &scratch);
     if (rc) return rc;
 
-    kgpu_tuning t;
-    {
-        std::lock_guard<std::mutex> lk(ctx->batch_mu);
-        t = ctx->tune;
-    }
-    const uint32_t threads = t.threads ? t.threads : 1024;
+    // batch_mu is held from validation to the event record, so a key deletion
+    // or a host unregistration either sees this batch's event or runs wholly
+    // before its validation
+    std::lock_guard<std::mutex> blk(ctx->batch_mu);
+    const kgpu_tuning t = ctx->tune;
+    uint32_t threads = t.threads ? t.threads : 1024;
     const uint32_t tile_chunks = t.tile_chunks ? t.tile_chunks : 32;
     const uint32_t ctas = t.ctas ? t.ctas : (uint32_t)ctx->num_sms;
+    // CBC encryption of host pages is staged only in the 512-thread kernel
+    if (threads > 512 && needs_staging(reqs, n)) threads = 512;
 
     std::lock_guard<std::mutex> lk(g_pack_mu);
     FixedRangeCache cache;
@@ -121,20 +144,25 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
     h->nreq = (uint32_t)n;
     h->tag = 0;
 
-    cudaStream_t s = (cudaStream_t)stream;
     BatchArgs a{};
     a.buf = scratch + kBatchOff;
     a.keys = ctx->d_keys;
     a.max_keys = ctx->cfg.max_keys;
     a.next_tile = reinterpret_cast<unsigned long long*>(scratch + kCounterOff);
     a.status = reinterpret_cast<int*>(scratch + kStatusOff);
+    // the first kStageWarps warps of the launch stage host-page CBC
+    // encryption; the others run it one lane per page (same bytes, slower)
+    a.scratch = reinterpret_cast<uint4*>(scratch + kStageOff);
+    a.scratch_warps = kStageWarps;
     // the counter and the status words must start at zero on every call
     if (cudaMemcpyAsync(scratch + kBatchOff, g_pack, batch_bytes((uint32_t)n), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         cudaMemsetAsync(scratch, 0, kStatusOff + n * sizeof(int), s) != cudaSuccess ||
-        launch_batch(a, (int)threads, (int)ctas, s) != cudaSuccess) {
+        launch_batch(a, (int)threads, (int)ctas, s) != cudaSuccess ||
+        cudaEventRecord(ctx->noalloc_done, s) != cudaSuccess) {
         cudaGetLastError();
         return KGPU_EIO;
     }
+    ctx->noalloc_issued = true;
     return KGPU_OK;
 }
