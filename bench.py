@@ -284,9 +284,10 @@ def batched_summary(b):
                             "p99_ms": _r(pl.get("p99_us", 0) / 1e3, 2)}}
 
 
-def serving_summary(sv, svh, rt):
+def serving_summary(sv, svh, rt, es=None):
     """p99 (us) of the serving ring and of one launch per request at each
-    offered rate, both residencies, plus the one-at-a-time 4 KiB round trip."""
+    offered rate, both residencies, the one-at-a-time 4 KiB round trip, and
+    the empty service's p50 at 512/1024/2048 threads (host pages)."""
     def p99(d):
         return _r((d.get("latency") or {}).get("p99_us"))
     out = {"rates_req_s": [r["rate_req_s"] for r in sv["rates"]],
@@ -298,6 +299,9 @@ def serving_summary(sv, svh, rt):
         out["ring_capacity_GB/s"] = _r(sv["ring_capacity"]["ring"]["GB/s"])
     out["roundtrip_4k_p50_p99_us"] = {k: [_r((rt[k]["latency"] or {}).get("p50_us")), p99(rt[k])]
                                       for k in ("ring", "launch", "host_ring", "host_launch")}
+    if es:
+        out["empty_4k_host_p50_us_512_1024_2048"] = {
+            form: [_r(es["host"][t][form]["p50_us"]) for t in ("512", "1024", "2048")] for form in ("ring", "launch")}
     return out
 
 
@@ -625,6 +629,130 @@ def run_roundtrip(ctx, kg, dev):
             "ring": {"rc": rc, "latency": pct(lat)}, "launch": {"rc": rc2, "latency": pct(lat2)},
             "host_ring": {"rc": rc3, "latency": pct(lat3)}, "host_launch": {"rc": rc4, "latency": pct(lat4)},
             "paper_context": "GTX 480 Non-Stop Kernel: 16.7 us (512 threads) for launch + 4 KB + wait"}
+
+
+def run_empty_service(ctx, kg, dev):
+    """The paper's Non-Stop Kernel measurement (section 3.1): one request at a
+    time carrying a 4 KiB input through a service that does no work (here it
+    copies the input through unchanged), timed on the host from submission
+    until the completion is seen, with 512, 1024 and 2048 threads taking part.
+    Ring: the request is split into 4096 / (threads / 32)-byte tiles, one warp
+    each, on the persistent serving kernel.  Launch: one plain launch of that
+    many threads per request.  Pages in registered pinned host memory (the
+    input crosses the host link, as the paper's did over PCIe) and in device
+    memory."""
+    import torch
+    n = 2000
+    data = w.seeded_bytes(8, w.STREAM_DATA, n * 4096)
+    bufs = {"host": (torch.from_numpy(data.copy()).pin_memory(), torch.zeros(n * 4096, dtype=torch.uint8).pin_memory()),
+            "device": (torch.from_numpy(data.copy()).to(f"cuda:{dev}"),
+                       torch.zeros(n * 4096, dtype=torch.uint8, device=f"cuda:{dev}"))}
+    for t in bufs["host"]:
+        ctx.host_register(t)
+    torch.cuda.synchronize()
+    arr = (np.arange(n) * 300_000).astype(np.uint64)
+    out = {"workload": "empty service (4 KiB copied through unchanged), one request at a time, 2000 requests "
+                       "300 us apart; latency from submission to the host seeing the completion",
+           "paper_context": "GTX 480 Non-Stop Kernel, launch + 4 KB + wait: 16.7 / 17.3 / 18.3 us at "
+                            "512 / 1024 / 2048 threads; 1.3x faster than a plain launch"}
+    try:
+        for where, (src, dst) in bufs.items():
+            flags = kg.REQ_SRC_HOST | kg.REQ_DST_HOST if where == "host" else 0
+            reqs = {}
+            for threads in (512, 1024, 2048):
+                r = np.zeros(n, dtype=kg.request_dtype())
+                r["mode"], r["len"], r["unit_size"], r["flags"] = kg.MODE_COPY, 4096, 4096 * 32 // threads, flags
+                r["src"] = src.data_ptr() + 4096 * np.arange(n)
+                r["dst"] = dst.data_ptr() + 4096 * np.arange(n)
+                reqs[threads] = r
+            rows = {t: {} for t in reqs}
+            ctx.serve_start()
+            try:
+                for t, r in reqs.items():
+                    rc, lat, _ = ctx.replay_serve(r, arr)
+                    rows[t]["ring"] = dict(pct(lat), rc=rc)
+            finally:
+                ctx.serve_stop(10_000_000_000)
+            for t, r in reqs.items():
+                rc, lat, _ = ctx.replay_launches(r, arr, nstreams=1)
+                rows[t]["launch"] = dict(pct(lat), rc=rc)
+            torch.cuda.synchronize()
+            if not np.array_equal(dst.cpu().numpy(), data):
+                raise SystemExit(f"empty service output differs from its input ({where} pages)")
+            out[where] = {str(t): v for t, v in rows.items()}
+    finally:
+        for t in bufs["host"]:
+            ctx.host_unregister(t)
+    return out
+
+
+def run_crossover(ctx, kg, dev):
+    """The paper's proposed start-up calibration (section 4): per mode and key
+    size, the request size from which the GPU is faster than the CPU.  Host-
+    resident pages: kgpu_calibrate_dispatch against a batch of one and against
+    the serving ring (the library's GPU legs) with OpenSSL AES on one host core
+    as the CPU leg.  Device-resident pages (AES-256-XTS): the GPU leg is one
+    request through the library; the CPU would first have to copy the pages
+    out of HBM and back, so its leg is copy-out + the host AES + copy-in."""
+    import torch
+    out = {"paper_context": "GTX 480 vs Core i7-930 kernel AES (ECB): GPU ahead from 8 KB (two pages)",
+           "cpu_leg": "OpenSSL libcrypto 3 EVP AES (AES-NI / Arm crypto extensions), one host thread"}
+    xo, pts = ctx.calibrate_dispatch()
+    out["host_pages_batch"] = {"crossover_bytes": xo["bytes"], "points": pts}
+    ctx.serve_start()
+    try:
+        xo, pts = ctx.calibrate_dispatch()
+    finally:
+        ctx.serve_stop(10_000_000_000)
+    out["host_pages_ring"] = {"crossover_bytes": xo["bytes"], "points": pts}
+    # device residency, AES-256-XTS, 4 KiB units
+    key = ctx.setkey(w.xts_key(9, 256), True)
+    big = 4 << 20
+    data = w.seeded_bytes(9, w.STREAM_DATA, big)
+    dsrc = torch.from_numpy(data.copy()).to(f"cuda:{dev}")
+    ddst = torch.empty_like(dsrc)
+    hsrc = torch.empty(big, dtype=torch.uint8).pin_memory()
+    hdst = torch.empty(big, dtype=torch.uint8).pin_memory()
+    for t in (hsrc, hdst):
+        ctx.host_register(t)
+    rows = []
+    try:
+        size = 4096
+        while size <= big:
+            reps = max(5, min(41, (2 << 20) // size)) | 1
+            rd = np.zeros(1, dtype=kg.request_dtype())
+            rd["mode"], rd["key"], rd["len"], rd["unit_size"] = kg.MODE_XTS, key, size, 4096
+            rd["src"], rd["dst"] = dsrc.data_ptr(), ddst.data_ptr()
+            rh = rd.copy()
+            rh["src"], rh["dst"], rh["flags"] = hsrc.data_ptr(), hdst.data_ptr(), kg.REQ_SRC_HOST | kg.REQ_DST_HOST
+            tg, tc = [], []
+            for i in range(reps + 1):
+                t0 = time.perf_counter()
+                st, _ = ctx.crypt(rd, kg.DISPATCH_GPU)
+                t1 = time.perf_counter()
+                hsrc[:size].copy_(dsrc[:size])
+                st2, _ = ctx.crypt(rh, kg.DISPATCH_HOST)
+                ddst[:size].copy_(hdst[:size])
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                if st or st2:
+                    raise SystemExit(f"crossover measurement failed: {st} {st2}")
+                if i:
+                    tg.append(t1 - t0)
+                    tc.append(t2 - t1)
+            rows.append({"bytes": size, "gpu_us": float(np.median(tg)) * 1e6, "cpu_with_copies_us": float(np.median(tc)) * 1e6})
+            size *= 2
+    finally:
+        for t in (hsrc, hdst):
+            ctx.host_unregister(t)
+        ctx.delkey(key)
+    cross = 2 * big
+    for r in reversed(rows):
+        if r["gpu_us"] >= r["cpu_with_copies_us"]:
+            break
+        cross = r["bytes"]
+    out["device_pages_xts256"] = {"crossover_bytes": cross, "points": rows}
+    return out
 
 
 def run_ecb_sweep(ctx, kg, dev):
@@ -963,8 +1091,15 @@ def run_kgpu(args):
         emit("serving_host", svh)
         rt = run_roundtrip(ctx, kg, dev)
         emit("roundtrip", rt)
-        line["serving"] = serving_summary(sv, svh, rt)
+        es = run_empty_service(ctx, kg, dev)
+        emit("empty_service", es)
+        line["serving"] = serving_summary(sv, svh, rt, es)
         emit("ecb_size_sweep", run_ecb_sweep(ctx, kg, dev))
+        xo = run_crossover(ctx, kg, dev)
+        emit("crossover", xo)
+        line["serving"]["crossover_host_ring_bytes"] = {
+            m: [xo["host_pages_ring"]["crossover_bytes"][m][k] for k in ("aes128", "aes256")]
+            for m in ("xts", "cbc_dec", "cbc_enc", "ecb")}
 
     if rank == 0 and not args.no_host and nbytes == GIB:
         emit("host_stream", run_host_stream(ctx, kg, kh, dev))

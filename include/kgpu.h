@@ -59,6 +59,7 @@ enum {
     KGPU_ENODEV = -19,     /* no such CUDA device, or not an sm_103 part */
     KGPU_EINVAL = -22,     /* malformed argument (length, alignment, key, mode) */
     KGPU_ENOENT = -2,      /* unknown key handle or ticket */
+    KGPU_ENOSYS = -38,     /* the host AES library (OpenSSL libcrypto 3) could not be loaded */
     KGPU_ETIMEDOUT = -110  /* a bounded wait ran out */
 };
 
@@ -68,7 +69,13 @@ enum {
     KGPU_MODE_XTS = 0,     /* XTS, direction from kgpu_request.dir */
     KGPU_MODE_CBC_DEC = 1, /* CBC decryption, parallel over blocks */
     KGPU_MODE_CBC_ENC = 2, /* CBC encryption, parallel over pages */
-    KGPU_MODE_ECB = 3      /* ECB, the paper's own service mode (section 3.3) */
+    KGPU_MODE_ECB = 3,     /* ECB, the paper's own service mode (section 3.3) */
+    KGPU_MODE_COPY = 4     /* the empty service: dst receives src unchanged, no key
+                              (the paper's round-trip measurement of its Non-Stop
+                              Kernel with a service that does no work, section 3.1);
+                              unit_size = bytes per tile, one warp per tile, so a
+                              request of len bytes occupies 32 * len / unit_size
+                              threads */
 };
 
 /* Library version, (major << 16) | minor. */
@@ -83,7 +90,9 @@ typedef struct kgpu_config {
     uint32_t ring_slots;          /* serving ring capacity (default 4096, power of two) */
     uint64_t admit_bytes;         /* serving: cap on bytes in flight (default 8 GiB) */
     uint64_t idle_timeout_ns;     /* serving kernel exits after this long with no work (default 2 s) */
-    uint32_t reserved[8];
+    uint32_t host_dispatch;       /* 1: measure the CPU/GPU crossover at kgpu_init and let kgpu_crypt
+                                     run small host-resident requests on the host (default 0: off) */
+    uint32_t reserved[7];
 } kgpu_config;
 
 /*
@@ -251,12 +260,14 @@ int kgpu_host_unregister(kgpu_ctx *ctx, void *ptr);
 typedef struct kgpu_request {
     uint32_t mode;       /* KGPU_MODE_* */
     uint32_t dir;        /* KGPU_ENCRYPT / KGPU_DECRYPT for XTS and ECB; ignored for CBC */
-    kgpu_key key;        /* an XTS key for KGPU_MODE_XTS, a single key otherwise */
+    kgpu_key key;        /* an XTS key for KGPU_MODE_XTS, a single key for CBC and ECB,
+                            ignored for KGPU_MODE_COPY */
     uint32_t flags;      /* KGPU_REQ_* bits, or 0 */
     const void *src;     /* 16-byte aligned */
     void *dst;           /* == src (in place) or disjoint from it */
     uint64_t len;        /* bytes: a multiple of unit_size (ECB: of 16) */
-    uint64_t unit_size;  /* XTS data-unit size / CBC page size; ignored for ECB */
+    uint64_t unit_size;  /* XTS data-unit size / CBC page size / COPY bytes per warp-tile;
+                            ignored for ECB */
     uint64_t sector;     /* XTS: number of the first data unit */
     const uint8_t *ivs;  /* CBC: len / unit_size IVs of 16 bytes, not overlapping dst */
 } kgpu_request;
@@ -448,6 +459,84 @@ int kgpu_replay_serve(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *a
                       int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns, uint64_t *detail);
 int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
                          uint32_t nstreams, int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
+
+/* ------------------------------------------------------------------------
+ * One request at a time, with CPU/GPU dispatch by a measured crossover.
+ *
+ * The paper finds its GPU AES slower than the CPU's below a request size of
+ * two pages, because a GPU request pays a fixed launch-and-copy cost, and
+ * proposes measuring that crossover when the system starts and sending
+ * smaller requests to the CPU (section 4).  kgpu_crypt is that dispatcher for
+ * one request, in the paper's request model (section 3.2: build a request,
+ * submit it, wait for it).  The host leg is AES-NI through OpenSSL's
+ * libcrypto (version 3, loaded at run time); it is a separate implementation,
+ * used only for requests whose every buffer is registered host memory, and
+ * only when a context was created with kgpu_config.host_dispatch = 1 (or when
+ * the caller forces it).
+ * ---------------------------------------------------------------------- */
+
+#define KGPU_DISPATCH_AUTO 0u /* host leg if enabled and len < the crossover, else GPU */
+#define KGPU_DISPATCH_GPU 1u  /* always the GPU leg */
+#define KGPU_DISPATCH_HOST 2u /* always the host leg (host-resident requests only) */
+
+/*
+ * Run one request (kgpu_request, any mode) and wait for it.  The GPU leg is
+ * the serving ring when kgpu_serve_start has started it, otherwise a batch of
+ * one request (kgpu_submit + kgpu_poll) on a stream of the context.  The host
+ * leg runs the request in the calling thread; it needs src and dst flagged
+ * KGPU_REQ_SRC_HOST / KGPU_REQ_DST_HOST (and KGPU_REQ_IVS_HOST for CBC), else
+ * KGPU_EINVAL.  With KGPU_DISPATCH_AUTO the host leg is taken when the context
+ * was created with host_dispatch = 1, the request is host-resident in that
+ * sense, and its length is below the measured crossover for its mode and key
+ * size (AES-128 / AES-192 and AES-256 measured as AES-128 and AES-256).
+ * Validation as kgpu_submit.  timeout_ns bounds the GPU leg's wait
+ * (KGPU_ETIMEDOUT; < 0 waits without limit).  *ran_on (if not NULL)
+ * receives KGPU_DISPATCH_GPU or KGPU_DISPATCH_HOST.  Returns the request's
+ * status: 0, or a negative KGPU_E* code (KGPU_ENOSYS if the host leg was
+ * forced and libcrypto is not available).
+ */
+int kgpu_crypt(kgpu_ctx *ctx, const kgpu_request *req, uint32_t dispatch, int64_t timeout_ns, uint32_t *ran_on);
+
+/* Where kgpu_crypt's host leg stops: requests shorter than bytes[mode][k]
+ * (mode KGPU_MODE_XTS..KGPU_MODE_ECB; k = 0 for AES-128, 1 for AES-256) run on
+ * the host.  form: the GPU leg that was measured (KGPU_DISPATCH_FORM_*). */
+#define KGPU_DISPATCH_FORM_BATCH 1u
+#define KGPU_DISPATCH_FORM_RING 2u
+typedef struct kgpu_crossover {
+    uint64_t bytes[4][2];
+    uint32_t form;
+    uint32_t valid; /* 1 once measured */
+} kgpu_crossover;
+
+/* One measured point of the calibration: both legs' median time for one
+ * request of `bytes` bytes, in registered pinned host memory. */
+typedef struct kgpu_dispatch_point {
+    uint32_t mode;     /* KGPU_MODE_XTS..KGPU_MODE_ECB */
+    uint32_t key_bits; /* 128 or 256 */
+    uint64_t bytes;
+    uint64_t host_ns;
+    uint64_t gpu_ns;
+} kgpu_dispatch_point;
+
+/*
+ * Measure the crossover now: for XTS, CBC decryption, CBC encryption and
+ * ECB, with AES-128 and AES-256 keys, and request sizes of 4 KiB to 4 MiB
+ * (powers of two) in registered pinned host memory, time kgpu_crypt's host
+ * leg and its GPU leg (the serving ring if it runs, else a batch of one) and
+ * record, per mode and key size, the smallest size from which the GPU leg is
+ * faster at every larger measured size (4 KiB if it is faster everywhere;
+ * 8 MiB if the host leg is faster everywhere).  The context's table is
+ * replaced, so call it again after kgpu_serve_start to route against the
+ * ring.  points (if not NULL) receives up to max_points measured points and
+ * *npoints their number (88 for the full sweep).  Allocates and frees its
+ * own buffers and keys.  Takes about a second.  Errors: KGPU_ENOSYS (no
+ * libcrypto), KGPU_ENOMEM, KGPU_EIO.
+ */
+int kgpu_calibrate_dispatch(kgpu_ctx *ctx, kgpu_dispatch_point *points, size_t max_points, size_t *npoints,
+                            kgpu_crossover *out);
+
+/* The context's current crossover table (valid = 0 before any calibration). */
+int kgpu_get_crossover(kgpu_ctx *ctx, kgpu_crossover *out);
 
 /* ------------------------------------------------------------------------
  * Allocation-free batched submission.  No counterpart in the paper.

@@ -22,11 +22,17 @@ MODE_XTS = 0
 MODE_CBC_DEC = 1
 MODE_CBC_ENC = 2
 MODE_ECB = 3
+MODE_COPY = 4  # the empty service: output = input, no key; unit_size = bytes per warp-tile
 
 _ERRORS = {
     -5: "EIO", -7: "E2BIG", -12: "ENOMEM", -14: "EFAULT", -16: "EBUSY", -19: "ENODEV", -22: "EINVAL", -2: "ENOENT",
-    -110: "ETIMEDOUT",
+    -110: "ETIMEDOUT", -38: "ENOSYS",
 }
+
+DISPATCH_AUTO = 0
+DISPATCH_GPU = 1
+DISPATCH_HOST = 2
+DISPATCH_FORM = {1: "batch", 2: "ring"}
 
 _lock = threading.Lock()
 _lib = None
@@ -92,7 +98,23 @@ class KgpuServeStats(ctypes.Structure):
 class KgpuConfig(ctypes.Structure):
     _fields_ = [("max_keys", ctypes.c_uint32), ("ring_slots", ctypes.c_uint32),
                 ("admit_bytes", ctypes.c_uint64), ("idle_timeout_ns", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint32 * 8)]
+                ("host_dispatch", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+
+
+class KgpuCrossover(ctypes.Structure):
+    """kgpu_crossover: requests shorter than bytes[mode][0: AES-128, 1: AES-256] run on the host."""
+    _fields_ = [("bytes", (ctypes.c_uint64 * 2) * 4), ("form", ctypes.c_uint32), ("valid", ctypes.c_uint32)]
+
+    def as_dict(self):
+        names = ("xts", "cbc_dec", "cbc_enc", "ecb")
+        return {"valid": bool(self.valid), "form": DISPATCH_FORM.get(self.form),
+                "bytes": {n: {"aes128": int(self.bytes[m][0]), "aes256": int(self.bytes[m][1])}
+                          for m, n in enumerate(names)}}
+
+
+class KgpuDispatchPoint(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("key_bits", ctypes.c_uint32), ("bytes", ctypes.c_uint64),
+                ("host_ns", ctypes.c_uint64), ("gpu_ns", ctypes.c_uint64)]
 
 
 def ensure_built() -> str:
@@ -142,6 +164,9 @@ def lib() -> ctypes.CDLL:
                 "kgpu_serve_submit_many": ([vp, vp, sz, vp, ctypes.POINTER(sz)], i32),
                 "kgpu_aes_xts_crypt_bitsliced": ([vp, u32, i32, vp, vp, sz, sz, u64, vp], i32),
                 "kgpu_host_unregister": ([vp, vp], i32),
+                "kgpu_crypt": ([vp, vp, u32, ctypes.c_int64, ctypes.POINTER(u32)], i32),
+                "kgpu_calibrate_dispatch": ([vp, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(KgpuCrossover)], i32),
+                "kgpu_get_crossover": ([vp, ctypes.POINTER(KgpuCrossover)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -350,6 +375,37 @@ def kgpu_autotune(ctx, reqs, stream=None, iters: int = 3):
     return best.as_dict(), ms.value
 
 
+def kgpu_crypt(ctx, req, dispatch=DISPATCH_AUTO, timeout_ns: int = -1):
+    """One request, run and waited for; returns (status, ran_on) where ran_on is
+    DISPATCH_GPU or DISPATCH_HOST.  A negative status is the request's error."""
+    ptr, n, keep = _req_array(req)
+    if n != 1:
+        raise ValueError("kgpu_crypt takes one request")
+    ran = ctypes.c_uint32(0)
+    rc = lib().kgpu_crypt(ctx, ptr, dispatch, timeout_ns, ctypes.byref(ran))
+    del keep
+    return rc, ran.value
+
+
+def kgpu_calibrate_dispatch(ctx, max_points: int = 128):
+    """Measure the CPU/GPU crossover now; returns (crossover dict, list of points)."""
+    pts = (KgpuDispatchPoint * max_points)()
+    n = ctypes.c_size_t(0)
+    xo = KgpuCrossover()
+    _check(lib().kgpu_calibrate_dispatch(ctx, pts, max_points, ctypes.byref(n), ctypes.byref(xo)),
+           "kgpu_calibrate_dispatch")
+    names = ("xts", "cbc_dec", "cbc_enc", "ecb")
+    points = [{"mode": names[p.mode], "key_bits": p.key_bits, "bytes": p.bytes, "host_ns": p.host_ns,
+               "gpu_ns": p.gpu_ns} for p in pts[: n.value]]
+    return xo.as_dict(), points
+
+
+def kgpu_get_crossover(ctx) -> dict:
+    xo = KgpuCrossover()
+    _check(lib().kgpu_get_crossover(ctx, ctypes.byref(xo)), "kgpu_get_crossover")
+    return xo.as_dict()
+
+
 NOALLOC_MAX_REQUESTS = 512
 
 
@@ -546,6 +602,15 @@ class Context:
 
     def autotune(self, reqs, stream=None, iters=3):
         return kgpu_autotune(self.handle, reqs, stream, iters)
+
+    def crypt(self, req, dispatch=DISPATCH_AUTO, timeout_ns=-1):
+        return kgpu_crypt(self.handle, req, dispatch, timeout_ns)
+
+    def calibrate_dispatch(self, max_points=128):
+        return kgpu_calibrate_dispatch(self.handle, max_points)
+
+    def crossover(self) -> dict:
+        return kgpu_get_crossover(self.handle)
 
     def submit_noalloc(self, reqs, stream=None, status=None):
         kgpu_submit_noalloc(self.handle, reqs, stream, status)

@@ -81,7 +81,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         libdir = os.path.join(cuda_home(), "lib")
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp,
-           "-Xlinker", f"-rpath={libdir}", "-L", libdir]
+           "-Xlinker", f"-rpath={libdir}", "-L", libdir, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -34,6 +34,7 @@ const char* kgpu_strerror(int code) {
         case KGPU_EINVAL: return "invalid argument";
         case KGPU_ENOENT: return "unknown key or ticket";
         case KGPU_ETIMEDOUT: return "bounded wait timed out";
+        case KGPU_ENOSYS: return "host AES library (libcrypto 3) not available";
         default: return "unknown error";
     }
 }
@@ -62,7 +63,8 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
     if (!ctx->cfg.ring_slots) ctx->cfg.ring_slots = 4096;
     if (!ctx->cfg.admit_bytes) ctx->cfg.admit_bytes = 8ull << 30;
     if (!ctx->cfg.idle_timeout_ns) ctx->cfg.idle_timeout_ns = 2000000000ull;
-    if (ctx->cfg.max_keys > (1u << 20) || (ctx->cfg.ring_slots & (ctx->cfg.ring_slots - 1))) {
+    if (ctx->cfg.max_keys > (1u << 20) || (ctx->cfg.ring_slots & (ctx->cfg.ring_slots - 1)) ||
+        ctx->cfg.host_dispatch > 1) {
         delete ctx;
         return KGPU_EINVAL;
     }
@@ -78,12 +80,18 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
     if (rc == KGPU_OK) rc = from_cuda(cudaMemset(ctx->d_keys, 0, sizeof(DevKey) * ctx->cfg.max_keys));
     if (rc == KGPU_OK) rc = from_cuda(cudaStreamCreateWithFlags(&ctx->key_stream, cudaStreamNonBlocking));
     if (rc == KGPU_OK) rc = from_cuda(cudaEventCreateWithFlags(&ctx->noalloc_done, cudaEventDisableTiming));
+    if (rc == KGPU_OK) rc = from_cuda(cudaStreamCreateWithFlags(&ctx->crypt_stream, cudaStreamNonBlocking));
     if (rc != KGPU_OK) {
         cudaGetLastError();
         kgpu_destroy(ctx);
         return rc;
     }
     ctx->keys.reserve(64);
+    // the paper's start-up calibration of the CPU/GPU crossover (section 4)
+    if (ctx->cfg.host_dispatch && (rc = kgpu_calibrate_dispatch(ctx, nullptr, 0, nullptr, nullptr)) != KGPU_OK) {
+        kgpu_destroy(ctx);
+        return rc;
+    }
     *out = ctx;
     return KGPU_OK;
 }
@@ -106,6 +114,7 @@ int kgpu_destroy(kgpu_ctx* ctx) {
             cudaEventDestroy(ctx->noalloc_done);
         }
         if (ctx->key_stream) cudaStreamDestroy(ctx->key_stream);
+        if (ctx->crypt_stream) cudaStreamDestroy(ctx->crypt_stream);
         if (ctx->d_keys) cudaFree(ctx->d_keys);
         for (const HostRange& r : ctx->hreg)
             if (r.owned) cudaHostUnregister(reinterpret_cast<void*>(r.base));

@@ -142,6 +142,11 @@ struct kgpu_ctx {
     cudaEvent_t noalloc_done = nullptr;
     bool noalloc_issued = false;
 
+    // kgpu_crypt: the measured crossover and the stream of its GPU leg's batches
+    std::mutex dispatch_mu;
+    kgpu_crossover xover{};
+    cudaStream_t crypt_stream = nullptr;
+
     // serving loop (kgpu_serve_*)
     std::mutex serve_mu;
     kgpu::ServeState serve;
@@ -335,7 +340,9 @@ constexpr uint32_t kReqFlagsAll = KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST | KGPU_R
 // count 32-block chunks; CBC decryption whole pages of about the same bytes;
 // CBC encryption 32 pages, one chain per lane.
 inline void set_tile_units(ReqDesc& d, uint32_t tile_chunks) {
-    if (d.mode == KGPU_MODE_CBC_ENC) {
+    if (d.mode == KGPU_MODE_COPY) {
+        d.tile_units = 1;  // the caller's unit_size is the tile
+    } else if (d.mode == KGPU_MODE_CBC_ENC) {
         d.tile_units = 32;
     } else if (d.mode == KGPU_MODE_CBC_DEC) {
         uint64_t ppt = (uint64_t)tile_chunks * 32 / d.unit_blocks;
@@ -364,7 +371,8 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
     if (q.flags & ~kReqFlagsAll) return KGPU_EINVAL;
     const bool cbc = q.mode == KGPU_MODE_CBC_DEC || q.mode == KGPU_MODE_CBC_ENC;
     const bool xts = q.mode == KGPU_MODE_XTS;
-    if (!xts && !cbc && q.mode != KGPU_MODE_ECB) return KGPU_EINVAL;
+    const bool copy = q.mode == KGPU_MODE_COPY;
+    if (!xts && !cbc && !copy && q.mode != KGPU_MODE_ECB) return KGPU_EINVAL;
     if ((xts || q.mode == KGPU_MODE_ECB) && q.dir != KGPU_ENCRYPT && q.dir != KGPU_DECRYPT) return KGPU_EINVAL;
     uint64_t unit = q.mode == KGPU_MODE_ECB ? 16 : q.unit_size;
     if (unit == 0 || unit % 16 || q.len % unit || unit / 16 > 0xFFFFFFFFull) return KGPU_EINVAL;
@@ -372,7 +380,7 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
         uint64_t units = q.len / unit;
         if (units && q.sector + (units - 1) < q.sector) return KGPU_EINVAL;
     }
-    {
+    if (!copy) {
         std::lock_guard<std::mutex> g(ctx->mu);
         if (q.key == 0 || q.key > ctx->keys.size()) return KGPU_ENOENT;
         const HostKey& k = ctx->keys[q.key - 1];
@@ -402,9 +410,9 @@ int make_desc(kgpu_ctx* ctx, const kgpu_request& q, Cache& rc, uint32_t tile_chu
     d->nblocks = q.len / 16;
     d->first_sector = q.sector;
     d->unit_blocks = (uint32_t)(unit / 16);
-    d->key = q.key - 1;
+    d->key = copy ? 0u : q.key - 1;
     d->mode = q.mode;
-    d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : q.dir;
+    d->dir = cbc ? (q.mode == KGPU_MODE_CBC_DEC ? 1u : 0u) : copy ? 0u : q.dir;
     d->flags = ((q.flags & KGPU_REQ_SRC_HOST) ? kDescSrcHost : 0u) | ((q.flags & KGPU_REQ_DST_HOST) ? kDescDstHost : 0u);
     set_tile_units(*d, tile_chunks);
     return KGPU_OK;

@@ -68,9 +68,11 @@ constexpr uint32_t kQuadPages = 8;
 constexpr uint32_t kStageBlocks = 8;
 constexpr size_t kStageWarpBytes = 32 * kStageBlocks * 16;
 
-// Work units of a request: XTS/ECB count 32-block chunks, CBC counts pages.
+// Work units of a request: XTS/ECB count 32-block chunks, CBC counts pages,
+// COPY counts its unit_size tiles.
 __host__ __device__ inline uint64_t request_units(const ReqDesc& d) {
-    if (d.mode == KGPU_MODE_CBC_DEC || d.mode == KGPU_MODE_CBC_ENC) return d.nblocks / d.unit_blocks;
+    if (d.mode == KGPU_MODE_CBC_DEC || d.mode == KGPU_MODE_CBC_ENC || d.mode == KGPU_MODE_COPY)
+        return d.nblocks / d.unit_blocks;
     return (d.nblocks + 31) / 32;
 }
 
@@ -180,6 +182,10 @@ inline uint64_t serve_max_tiles(uint64_t tile_ring) { return tile_ring / 2; }
 // Launch entry points of the unified kernels (kgpu_unified.cu).  They return
 // a cudaError_t from the launch.
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s);
+// The empty service as one plain launch: warp w copies unit w (unit_blocks
+// blocks); 32 threads per unit, in CTAs of up to 1024 threads.
+cudaError_t launch_copy(const uint4* src, uint4* dst, uint64_t nblocks, uint32_t unit_blocks, int num_sms,
+                        cudaStream_t s);
 const void* batch_kernel_fn(int threads);  // for CUDA-graph kernel nodes
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s);
 cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas,

@@ -761,15 +761,18 @@ int kgpu_replay_launches(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t
             if (rc) break;
         }
         const ReqDesc& d = descs[i];
-        const HostKey& k = keys[d.key];
         cudaStream_t s = streams[i % nstreams];
         cudaError_t e;
-        if (d.mode == KGPU_MODE_XTS || d.mode == KGPU_MODE_ECB) {
+        if (d.mode == KGPU_MODE_COPY) {
+            e = launch_copy(d.src, d.dst, d.nblocks, d.unit_blocks, ctx->num_sms, s);
+        } else if (d.mode == KGPU_MODE_XTS || d.mode == KGPU_MODE_ECB) {
+            const HostKey& k = keys[d.key];
             BulkParams p;
             fill_bulk(&p, k, (int)d.dir, d.src, d.dst, d.nblocks * 16, (size_t)d.unit_blocks * 16, d.first_sector);
             e = d.mode == KGPU_MODE_XTS ? launch_xts(p, k.nr, (int)d.dir, ctx->num_sms, s)
                                         : launch_ecb(p, k.nr, (int)d.dir, ctx->num_sms, s);
         } else {
+            const HostKey& k = keys[d.key];
             CbcParams p;
             std::memset(&p, 0, sizeof(p));
             p.src = d.src;

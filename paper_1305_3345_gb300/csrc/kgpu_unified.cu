@@ -12,6 +12,8 @@
 // and run the tile.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "aes_device.cuh"
 #include "kgpu_internal.h"
 
@@ -365,10 +367,22 @@ __device__ __forceinline__ uint32_t find_request(const uint64_t* tile_start, uin
 // stage: this warp's scratch area, or null.  QUAD: compile the four-lanes-per-
 // page CBC encryption in (only the serving kernel's descriptors ask for it,
 // and it would cost the batch kernels registers).
+// The empty service (KGPU_MODE_COPY): units [u0, u1) of unit_blocks blocks
+// each are copied through unchanged, one 16-byte access per lane per step.
+__device__ __forceinline__ void tile_copy(const ReqDesc& d, uint64_t u0, uint64_t u1) {
+    const uint64_t b1 = u1 * d.unit_blocks;
+    for (uint64_t b = u0 * d.unit_blocks + lane_id(); b < b1; b += 32) d.dst[b] = d.src[b];
+}
+
 template <bool QUAD>
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
                                      WarpKeys& K, uint32_t& cur_sel, uint4* stage) {
     const uint32_t lane = lane_id();
+    if (d.mode == KGPU_MODE_COPY) {
+        const uint64_t u0 = tile_in_req * d.tile_units, units = request_units(d);
+        tile_copy(d, u0, u0 + d.tile_units < units ? u0 + d.tile_units : units);
+        return 0;
+    }
     if (d.key >= max_keys) return KGPU_ENOENT;
     const DevKey& dk = keys[d.key];
     const bool is_xts = d.mode == KGPU_MODE_XTS;
@@ -764,6 +778,31 @@ cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s) {
     if (threads != kServeThreads) return cudaErrorInvalidValue;
     serve_kernel<kServeThreads><<<grid, kServeThreads, unified_smem_bytes(kServeThreads), s>>>(a);
+    return cudaGetLastError();
+}
+
+// The empty service as a plain launch: warp w (of the whole grid) copies
+// units w, w + warps, ...
+__global__ void __launch_bounds__(1024) copy_kernel(const uint4* src, uint4* dst, uint64_t units,
+                                                    uint32_t unit_blocks) {
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < units; w += warps) {
+        const uint64_t b1 = (w + 1) * unit_blocks;
+        for (uint64_t b = w * unit_blocks + (threadIdx.x & 31); b < b1; b += 32) dst[b] = src[b];
+    }
+}
+
+cudaError_t launch_copy(const uint4* src, uint4* dst, uint64_t nblocks, uint32_t unit_blocks, int num_sms,
+                        cudaStream_t s) {
+    if (!unit_blocks || nblocks % unit_blocks) return cudaErrorInvalidValue;
+    const uint64_t units = nblocks / unit_blocks;
+    if (!units) return cudaSuccess;
+    // 32 threads per unit: one CTA of up to 1024 threads, else CTAs of 1024
+    // (at most 32 per SM; larger requests loop)
+    const int threads = units * 32 <= 1024 ? (int)(units * 32) : 1024;
+    const uint64_t ctas = (units * 32 + threads - 1) / threads;
+    const int grid = (int)std::min<uint64_t>(ctas, (uint64_t)num_sms * 32);
+    copy_kernel<<<grid, threads, 0, s>>>(src, dst, units, unit_blocks);
     return cudaGetLastError();
 }
 
