@@ -270,6 +270,25 @@ def compact(obj, sig=5):
     return obj
 
 
+def stage_split(stages, sel=None):
+    """p50/p99 (us) of each stage of the serving request path, from
+    kgpu_replay_serve_stages' per-request record (ns since arrival): host
+    queueing until published, published -> dispatcher took it, -> tiles
+    published, -> first tile started, -> completed, -> host saw it."""
+    s = np.asarray(stages, dtype=np.int64)
+    if sel is not None:
+        s = s[sel]
+    ok = (s[:, 1:5] != np.iinfo(np.int64).min).all(axis=1)
+    s = s[ok]
+    if not len(s):
+        return None
+    names = ("host_queue", "to_dispatcher", "dispatch", "to_first_tile", "service", "to_host")
+    d = np.stack([s[:, 0], s[:, 1] - s[:, 0], s[:, 2] - s[:, 1], s[:, 3] - s[:, 2], s[:, 4] - s[:, 3],
+                  s[:, 5] - s[:, 4]], axis=1).astype(np.float64) / 1e3
+    return {n: {"p50_us": round(float(np.percentile(d[:, k], 50)), 2), "p99_us": round(float(np.percentile(d[:, k], 99)), 2)}
+            for k, n in enumerate(names)}
+
+
 def _r(x, nd=1):
     return None if x is None else round(float(x), nd)
 
@@ -425,31 +444,31 @@ def run_serving(ctx, kg, dev, seconds, host=False):
             reqs["flags"] = np.where(mix.modes == w.MODE_XTS, kg.REQ_SRC_HOST | kg.REQ_DST_HOST,
                                      kg.REQ_SRC_HOST | kg.REQ_DST_HOST | kg.REQ_IVS_HOST)
         arr = (w.poisson_arrivals(5 + rate, n, float(rate)) * 1e9).astype(np.uint64)
-        detail = np.zeros(3 * n, dtype=np.uint64)
         ctx.serve_start(admit_bytes=8 * GIB)
         try:
             with ClockSampler(dev) as clk_ring:
-                rc, lat, wall = ctx.replay_serve(reqs, arr, timeout_ns=120_000_000_000, detail=detail)
+                rc, lat, wall, stg, _ = ctx.replay_serve_stages(reqs, arr, timeout_ns=120_000_000_000)
             stats = ctx.serve_stats()
         finally:
             ctx.serve_stop(30_000_000_000)
-        d = detail.reshape(n, 3).astype(np.int64)
         # device stamps lost to a slot that retired a later request before the
-        # host looked (0, 0) are left out of the device-service figures
-        stamped = (d[:, 1] > 0) & (d[:, 2] >= d[:, 1])
-        service = d[:, 2] - d[:, 1]
+        # host looked are left out of the device-service and stage figures
+        stamped = (stg[:, 1:5] != np.iinfo(np.int64).min).all(axis=1)
+        service = stg[:, 4] - stg[:, 3]
         by_mode = {}
         for m, name in ((w.MODE_XTS, "xts"), (w.MODE_CBC_DEC, "cbc_dec"), (w.MODE_CBC_ENC, "cbc_enc")):
             sel = mix.modes == m
             if sel.any():
-                by_mode[name] = {"latency": pct(lat[sel]), "device_service": pct(service[sel & stamped])}
+                by_mode[name] = {"latency": pct(lat[sel]), "device_service": pct(service[sel & stamped]),
+                                 "stages": stage_split(stg, sel)}
         with ClockSampler(dev) as clk_pr:
             rc2, lat2, wall2 = ctx.replay_launches(reqs, arr, nstreams=8, timeout_ns=120_000_000_000)
         total = int(mix.sizes.sum())
         res.append({
             "rate_req_s": rate, "requests": n, "offered_GB/s": total / (float(arr[-1]) / 1e9) / 1e9,
             "ring": {"GB/s": total / (wall / 1e9) / 1e9, "rc": rc, "latency": pct(lat),
-                     "host_wait_before_publish": pct(d[:, 0]), "device_service": pct(service[stamped]),
+                     "host_wait_before_publish": pct(stg[:, 0]), "device_service": pct(service[stamped]),
+                     "stages": stage_split(stg),
                      "device_stamps_lost": int(n - stamped.sum()),
                      "by_mode": by_mode, "clocks": clk_ring.summary(),
                      "busy_refusals": stats["busy_refusals"], "launches": stats["launches"]},
@@ -601,7 +620,7 @@ def run_roundtrip(ctx, kg, dev):
     torch.cuda.synchronize()
     ctx.serve_start()
     try:
-        rc, lat, _ = ctx.replay_serve(r, arr)
+        rc, lat, _, stg, _ = ctx.replay_serve_stages(r, arr)
     finally:
         ctx.serve_stop(10_000_000_000)
     rc2, lat2, _ = ctx.replay_launches(r, arr, nstreams=1)
@@ -617,7 +636,7 @@ def run_roundtrip(ctx, kg, dev):
     rh["flags"] = kg.REQ_SRC_HOST | kg.REQ_DST_HOST
     ctx.serve_start()
     try:
-        rc3, lat3, _ = ctx.replay_serve(rh, arr)
+        rc3, lat3, _, stg3, _ = ctx.replay_serve_stages(rh, arr)
     finally:
         ctx.serve_stop(10_000_000_000)
     rc4, lat4, _ = ctx.replay_launches(rh, arr, nstreams=1)
@@ -626,8 +645,10 @@ def run_roundtrip(ctx, kg, dev):
     ctx.delkey(key)
     return {"workload": "4 KiB AES-256-XTS requests, one in flight at a time, 2000 requests; "
                         "pages in device memory, and in registered pinned host memory (host_*)",
-            "ring": {"rc": rc, "latency": pct(lat)}, "launch": {"rc": rc2, "latency": pct(lat2)},
-            "host_ring": {"rc": rc3, "latency": pct(lat3)}, "host_launch": {"rc": rc4, "latency": pct(lat4)},
+            "ring": {"rc": rc, "latency": pct(lat), "stages": stage_split(stg)},
+            "launch": {"rc": rc2, "latency": pct(lat2)},
+            "host_ring": {"rc": rc3, "latency": pct(lat3), "stages": stage_split(stg3)},
+            "host_launch": {"rc": rc4, "latency": pct(lat4)},
             "paper_context": "GTX 480 Non-Stop Kernel: 16.7 us (512 threads) for launch + 4 KB + wait"}
 
 
@@ -669,8 +690,8 @@ def run_empty_service(ctx, kg, dev):
             ctx.serve_start()
             try:
                 for t, r in reqs.items():
-                    rc, lat, _ = ctx.replay_serve(r, arr)
-                    rows[t]["ring"] = dict(pct(lat), rc=rc)
+                    rc, lat, _, stg, off = ctx.replay_serve_stages(r, arr)
+                    rows[t]["ring"] = dict(pct(lat), rc=rc, stages=stage_split(stg))
             finally:
                 ctx.serve_stop(10_000_000_000)
             for t, r in reqs.items():

@@ -460,6 +460,28 @@ int kgpu_replay_serve(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *a
 int kgpu_replay_launches(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
                          uint32_t nstreams, int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns);
 
+/*
+ * kgpu_replay_serve, also splitting each request's latency by stage of the
+ * request path (the paper's message passing between the host and a resident
+ * kernel, section 3.1).  stages[6 * i ...] receives, in nanoseconds since
+ * request i's arrival on the host clock: [0] the host published it (the ring
+ * head store), [1] the device's dispatcher took it, [2] its tiles were
+ * published to the workers, [3] its first tile started, [4] it completed on
+ * the device, [5] the host saw it complete (= latency_ns[i]).  Entries 1-4
+ * are device %globaltimer stamps moved to the host clock by an offset
+ * estimated from the dispatcher's heartbeat before and after the run and
+ * interpolated between the two (in case the clocks' rates differ);
+ * clock_offset_ns, if not NULL, receives the two estimates (host time =
+ * device time + offset).  Each estimate includes the shortest device-to-host
+ * store latency, so those entries read late by that much (under a
+ * microsecond).  A stamp lost to a slot that retired a later request before
+ * the host looked is INT64_MIN.  Starts the serving kernel first if it is
+ * not running.
+ */
+int kgpu_replay_serve_stages(kgpu_ctx *ctx, const kgpu_request *reqs, const uint64_t *arrival_ns, size_t n,
+                             int64_t timeout_ns, uint64_t *latency_ns, uint64_t *wall_ns, int64_t *stages,
+                             int64_t *clock_offset_ns);
+
 /* ------------------------------------------------------------------------
  * One request at a time, with CPU/GPU dispatch by a measured crossover.
  *

@@ -165,6 +165,8 @@ def lib() -> ctypes.CDLL:
                 "kgpu_aes_xts_crypt_bitsliced": ([vp, u32, i32, vp, vp, sz, sz, u64, vp], i32),
                 "kgpu_host_unregister": ([vp, vp], i32),
                 "kgpu_crypt": ([vp, vp, u32, ctypes.c_int64, ctypes.POINTER(u32)], i32),
+                "kgpu_replay_serve_stages": ([vp, vp, vp, sz, ctypes.c_int64, vp, ctypes.POINTER(u64), vp,
+                                              ctypes.POINTER(ctypes.c_int64)], i32),
                 "kgpu_calibrate_dispatch": ([vp, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(KgpuCrossover)], i32),
                 "kgpu_get_crossover": ([vp, ctypes.POINTER(KgpuCrossover)], i32),
             }
@@ -532,6 +534,28 @@ def kgpu_replay_serve(ctx, reqs, arrival_ns, timeout_ns: int = 60_000_000_000, d
     return _replay(lib().kgpu_replay_serve, ctx, reqs, arrival_ns, (), timeout_ns, detail)
 
 
+STAGE_NAMES = ("published", "dispatcher_took", "tiles_published", "first_tile", "completed", "seen")
+STAGE_LOST = -(1 << 63)
+
+
+def kgpu_replay_serve_stages(ctx, reqs, arrival_ns, timeout_ns: int = 60_000_000_000):
+    """Replay through the serving ring with each request's latency split by
+    stage: (rc, latency_ns, wall_ns, stages, (clock offset before, after)) where stages is
+    an int64 (n, 6) array of ns since arrival (STAGE_NAMES; STAGE_LOST where a
+    device stamp was lost)."""
+    import numpy as np
+    ptr, n, keep = _req_array(reqs)
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+    lat = np.zeros(n, dtype=np.uint64)
+    stages = np.zeros((n, 6), dtype=np.int64)
+    wall = ctypes.c_uint64()
+    off = (ctypes.c_int64 * 2)()
+    rc = lib().kgpu_replay_serve_stages(ctx, ptr, arr.ctypes.data, n, timeout_ns, lat.ctypes.data,
+                                        ctypes.byref(wall), stages.ctypes.data, off)
+    del keep
+    return rc, lat, wall.value, stages, (off[0], off[1])
+
+
 def kgpu_replay_launches(ctx, reqs, arrival_ns, nstreams: int = 8, timeout_ns: int = 60_000_000_000):
     """Open-loop replay with one kernel launch per request: (rc, latency_ns, wall_ns)."""
     return _replay(lib().kgpu_replay_launches, ctx, reqs, arrival_ns, (nstreams,), timeout_ns)
@@ -641,6 +665,9 @@ class Context:
 
     def replay_serve(self, reqs, arrival_ns, timeout_ns=60_000_000_000, detail=None):
         return kgpu_replay_serve(self.handle, reqs, arrival_ns, timeout_ns, detail)
+
+    def replay_serve_stages(self, reqs, arrival_ns, timeout_ns=60_000_000_000):
+        return kgpu_replay_serve_stages(self.handle, reqs, arrival_ns, timeout_ns)
 
     def replay_launches(self, reqs, arrival_ns, nstreams=8, timeout_ns=60_000_000_000):
         return kgpu_replay_launches(self.handle, reqs, arrival_ns, nstreams, timeout_ns)

@@ -69,14 +69,16 @@ struct ServeState {
     bool running = false;  // a kernel instance was launched and has not been seen to exit
     cudaStream_t stream = nullptr;
     cudaEvent_t kdone = nullptr;
-    uint8_t* host_mem = nullptr;  // pinned, mapped: hdr | slots | done_seq | status | t_start | t_done
+    uint8_t* host_mem = nullptr;  // pinned, mapped: hdr | slots | done_seq | status | stamps
     uint8_t* dev_mem = nullptr;   // ServeDev | claim | fin
     ServeHostHdr* hdr = nullptr;
     ServeSlot* slots = nullptr;
     unsigned long long* done_seq = nullptr;
     int* status = nullptr;
-    unsigned long long* t_start = nullptr;
-    unsigned long long* t_done = nullptr;
+    // the device's %globaltimer stamps of each slot's request: [0] dispatcher
+    // took it, [1] tiles published, [2] first tile started, [3] completed
+    static constexpr int kStamps = 4;
+    unsigned long long* stamp[kStamps] = {};
     ServeArgs args{};
     uint32_t nslots = 0;
     uint64_t tile_ring = 0;  // entries of the device tile ring
@@ -95,11 +97,12 @@ struct ServeState {
     // by reap -- always before the slot is staged again -- so a late reader
     // still finds it.  ret_seq[s] is the record's sequence lock (UINT64_MAX
     // while reap rewrites it).
-    std::vector<uint64_t> ret_seq, ret_t_start, ret_t_done;
+    std::vector<uint64_t> ret_seq, ret_stamp[kStamps];
     std::vector<int> ret_status;
     std::map<uint64_t, int> failed;  // seq -> KGPU_E* of failed requests (the newest kFailedKept)
     uint64_t submitted = 0, completed = 0, busy_refusals = 0, launches = 0;
     uint64_t last_alive_check = 0;  // ns; publish re-checks the kernel at most every 20 us
+    uint64_t last_publish_ns = 0;   // host time of the newest ring-head store
     unsigned last_exit = 0;
 };
 

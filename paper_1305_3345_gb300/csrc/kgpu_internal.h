@@ -124,7 +124,9 @@ struct ServeSlot {
     unsigned long long ntiles;  // tiles of this request
     unsigned long long seq;     // request number (slot = seq & mask)
     unsigned long long pos0;    // device copy only: tile-ring position of its first tile
-    unsigned long long pad[5];
+    unsigned long long t_disp;  // device copy only: %globaltimer when the dispatcher took it
+    unsigned long long t_pub;   // device copy only: %globaltimer when its tiles were published
+    unsigned long long pad[3];
 };
 static_assert(sizeof(ServeSlot) == 128, "slot layout");
 
@@ -156,6 +158,8 @@ struct ServeArgs {
     int* status;                      // [S], mapped host
     unsigned long long* t_start;      // [S], mapped host: %globaltimer when its first tile starts
     unsigned long long* t_done;       // [S], mapped host: %globaltimer at completion
+    unsigned long long* t_disp;       // [S], mapped host: %globaltimer when the dispatcher took it
+    unsigned long long* t_pub;        // [S], mapped host: %globaltimer when its tiles were published
     ServeDev* dev;
     ServeSlot* dslots;                // [S], device copy of the descriptors
     unsigned long long* fin;          // [S], device: tiles finished per request

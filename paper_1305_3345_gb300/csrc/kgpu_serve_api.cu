@@ -19,6 +19,10 @@ using namespace kgpu::hostutil;
 
 namespace {
 
+// Words per request of kgpu_replay_serve_stages: published, dispatcher took
+// it, tiles published, first tile started, completed, seen by the host.
+constexpr size_t kStageWords = 6;
+
 uint64_t now_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -68,9 +72,8 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     const size_t o_slots = 128;
     const size_t o_done = o_slots + (size_t)S * sizeof(ServeSlot);
     const size_t o_status = o_done + (size_t)S * 8;
-    const size_t o_tstart = align_up(o_status + (size_t)S * 4, 128);
-    const size_t o_tdone = o_tstart + (size_t)S * 8;
-    const size_t host_bytes = o_tdone + (size_t)S * 8;
+    const size_t o_stamps = align_up(o_status + (size_t)S * 4, 128);  // kStamps arrays of S words
+    const size_t host_bytes = o_stamps + (size_t)ServeState::kStamps * S * 8;
     // tile ring: room for every tile admission allows in flight, plus slack
     uint64_t want = st.admit_bytes / ((uint64_t)st.tile_chunks * 512) + 2ull * S;
     uint64_t T = 1ull << 16;
@@ -103,8 +106,8 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     st.slots = reinterpret_cast<ServeSlot*>(st.host_mem + o_slots);
     st.done_seq = reinterpret_cast<unsigned long long*>(st.host_mem + o_done);
     st.status = reinterpret_cast<int*>(st.host_mem + o_status);
-    st.t_start = reinterpret_cast<unsigned long long*>(st.host_mem + o_tstart);
-    st.t_done = reinterpret_cast<unsigned long long*>(st.host_mem + o_tdone);
+    for (int k = 0; k < ServeState::kStamps; k++)
+        st.stamp[k] = reinterpret_cast<unsigned long long*>(st.host_mem + o_stamps + (size_t)k * S * 8);
 
     ServeArgs& a = st.args;
     a = ServeArgs{};
@@ -112,8 +115,10 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     a.hh = reinterpret_cast<ServeHostHdr*>(dmap);
     a.done_seq = reinterpret_cast<unsigned long long*>(dmap + o_done);
     a.status = reinterpret_cast<int*>(dmap + o_status);
-    a.t_start = reinterpret_cast<unsigned long long*>(dmap + o_tstart);
-    a.t_done = reinterpret_cast<unsigned long long*>(dmap + o_tdone);
+    a.t_disp = reinterpret_cast<unsigned long long*>(dmap + o_stamps);
+    a.t_pub = reinterpret_cast<unsigned long long*>(dmap + o_stamps + (size_t)S * 8);
+    a.t_start = reinterpret_cast<unsigned long long*>(dmap + o_stamps + (size_t)2 * S * 8);
+    a.t_done = reinterpret_cast<unsigned long long*>(dmap + o_stamps + (size_t)3 * S * 8);
     a.dev = reinterpret_cast<ServeDev*>(st.dev_mem);
     a.dslots = reinterpret_cast<ServeSlot*>(st.dev_mem + d_slots);
     a.fin = reinterpret_cast<unsigned long long*>(st.dev_mem + d_fin);
@@ -135,8 +140,7 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     st.slot_len.assign(S, 0);
     st.slot_gen.assign(S, UINT64_MAX);
     st.ret_seq.assign(S, UINT64_MAX);
-    st.ret_t_start.assign(S, 0);
-    st.ret_t_done.assign(S, 0);
+    for (auto& r : st.ret_stamp) r.assign(S, 0);
     st.ret_status.assign(S, 0);
     st.failed.clear();
     st.outstanding.clear();
@@ -190,8 +194,8 @@ void reap(ServeState& st) {
             __atomic_store_n(&st.ret_seq[s], UINT64_MAX, __ATOMIC_RELAXED);
             __atomic_thread_fence(__ATOMIC_RELEASE);
             __atomic_store_n(&st.ret_status[s], code, __ATOMIC_RELAXED);
-            __atomic_store_n(&st.ret_t_start[s], (uint64_t)load_acquire(&st.t_start[s]), __ATOMIC_RELAXED);
-            __atomic_store_n(&st.ret_t_done[s], (uint64_t)load_acquire(&st.t_done[s]), __ATOMIC_RELAXED);
+            for (int k = 0; k < ServeState::kStamps; k++)
+                __atomic_store_n(&st.ret_stamp[k][s], (uint64_t)load_acquire(&st.stamp[k][s]), __ATOMIC_RELAXED);
             __atomic_store_n(&st.ret_seq[s], seq, __ATOMIC_RELEASE);
             if (code) {
                 st.failed[seq] = code;
@@ -211,28 +215,28 @@ void reap(ServeState& st) {
 // complete (done_seq of its slot >= seq + 1, acquire), without serve_mu: from
 // the slot's mapped words while the slot still holds seq, else from reap's
 // record of it.  false when the slot has since retired a later request too.
-bool read_completed(const ServeState& st, uint64_t seq, int* status, uint64_t* t_start, uint64_t* t_done) {
+// stamps: ServeState::kStamps words (dispatcher took it, tiles published,
+// first tile started, completed).
+bool read_completed(const ServeState& st, uint64_t seq, int* status, uint64_t* stamps) {
     const uint32_t s = (uint32_t)(seq & (st.nslots - 1));
+    uint64_t v[ServeState::kStamps];
     if (__atomic_load_n(&st.slot_gen[s], __ATOMIC_ACQUIRE) == seq) {
         const int c = load_acquire(&st.status[s]);
-        const uint64_t a = load_acquire(&st.t_start[s]), b = load_acquire(&st.t_done[s]);
+        for (int k = 0; k < ServeState::kStamps; k++) v[k] = load_acquire(&st.stamp[k][s]);
         __atomic_thread_fence(__ATOMIC_ACQUIRE);
         if (__atomic_load_n(&st.slot_gen[s], __ATOMIC_RELAXED) == seq) {
             *status = c;
-            *t_start = a;
-            *t_done = b;
+            for (int k = 0; k < ServeState::kStamps; k++) stamps[k] = v[k];
             return true;
         }
     }
     if (__atomic_load_n(&st.ret_seq[s], __ATOMIC_ACQUIRE) == seq) {
         const int c = __atomic_load_n(&st.ret_status[s], __ATOMIC_RELAXED);
-        const uint64_t a = __atomic_load_n(&st.ret_t_start[s], __ATOMIC_RELAXED);
-        const uint64_t b = __atomic_load_n(&st.ret_t_done[s], __ATOMIC_RELAXED);
+        for (int k = 0; k < ServeState::kStamps; k++) v[k] = __atomic_load_n(&st.ret_stamp[k][s], __ATOMIC_RELAXED);
         __atomic_thread_fence(__ATOMIC_ACQUIRE);
         if (__atomic_load_n(&st.ret_seq[s], __ATOMIC_RELAXED) == seq) {
             *status = c;
-            *t_start = a;
-            *t_done = b;
+            for (int k = 0; k < ServeState::kStamps; k++) stamps[k] = v[k];
             return true;
         }
     }
@@ -263,10 +267,11 @@ constexpr uint32_t kBacklogTileChunks = 64;  // 32 KiB
 // it gets 32-KiB tiles: per tile the workers claim a position, reload a key
 // schedule and (for XTS) run a 32-unit tweak batch, and on small tiles those
 // costs cap the ring's throughput.  A ring that keeps up keeps the configured
-// (default 2-KiB) tiles and their lower latency, and runs CBC encryption of
-// device pages four lanes to a page (twice the chain speed, a quarter of the
-// pages per warp).  The check is one load of a completion word, whatever the
-// number of requests in flight.
+// (default 2-KiB) tiles and their lower latency, and runs CBC encryption four
+// lanes to a page (twice the chain speed, a quarter of the pages per warp;
+// host pages through the warp's scratch area, whole lines at a time).  The
+// check is one load of a completion word, whatever the number of requests in
+// flight.
 bool backlogged(const ServeState& st) {
     const uint64_t q = st.nslots / 4;
     if (st.next_seq < q) return false;
@@ -278,9 +283,11 @@ int stage(ServeState& st, const ReqDesc& dreq, uint64_t* seq_out) {
     ReqDesc d = dreq;
     if (backlogged(st)) {
         set_tile_units(d, std::max<uint32_t>(st.tile_chunks, kBacklogTileChunks));
-    } else if (d.mode == KGPU_MODE_CBC_ENC && !(d.flags & (kDescSrcHost | kDescDstHost))) {
+    } else if (d.mode == KGPU_MODE_CBC_ENC &&
+               (!(d.flags & (kDescSrcHost | kDescDstHost)) || d.unit_blocks % kStageBlocks == 0)) {
         // a CBC-encryption request's latency is its chain time: while the ring
-        // keeps up, four lanes share each page's chain (8 pages a warp)
+        // keeps up, four lanes share each page's chain (8 pages a warp); host
+        // pages take the staged form of it, which needs whole 128-byte lines
         d.flags |= kDescQuad;
         d.tile_units = kQuadPages;
     }
@@ -308,8 +315,7 @@ int stage(ServeState& st, const ReqDesc& dreq, uint64_t* seq_out) {
     __atomic_store_n(&st.slot_gen[s], UINT64_MAX, __ATOMIC_RELAXED);
     __atomic_thread_fence(__ATOMIC_RELEASE);
     __atomic_store_n(&st.status[s], 0, __ATOMIC_RELAXED);
-    __atomic_store_n(&st.t_start[s], 0ull, __ATOMIC_RELAXED);
-    __atomic_store_n(&st.t_done[s], 0ull, __ATOMIC_RELAXED);
+    for (int k = 0; k < ServeState::kStamps; k++) __atomic_store_n(&st.stamp[k][s], 0ull, __ATOMIC_RELAXED);
     __atomic_store_n(&st.slot_gen[s], seq, __ATOMIC_RELEASE);
     st.slot_busy[s] = 1;
     st.slot_seq[s] = seq;
@@ -328,6 +334,7 @@ int stage(ServeState& st, const ReqDesc& dreq, uint64_t* seq_out) {
 int commit(kgpu_ctx* ctx, ServeState& st) {
     store_release(&st.hdr->head, (unsigned long long)st.next_seq);
     const uint64_t t = now_ns();
+    st.last_publish_ns = t;
     if (!st.running || t - st.last_alive_check > 20000) {
         st.last_alive_check = t;
         return ensure_running(ctx, st);
@@ -452,19 +459,19 @@ int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* 
         const unsigned long long d = load_acquire(&st.done_seq[s]);
         if (d >= seq + 1) {
             int code = 0;
-            uint64_t a = 0, b = 0;
-            if (!read_completed(st, seq, &code, &a, &b)) {
+            uint64_t v[ServeState::kStamps] = {};
+            if (!read_completed(st, seq, &code, v)) {
                 // its slot has retired a later request too: stamps are gone,
                 // a failure code is kept by ticket
                 std::lock_guard<std::mutex> lk(ctx->serve_mu);
                 auto f = st.failed.find(seq);
                 code = f != st.failed.end() ? f->second : 0;
-                a = b = 0;
+                for (auto& x : v) x = 0;
             }
             if (status) *status = code;
             if (stamps) {
-                stamps[0] = a;
-                stamps[1] = b;
+                stamps[0] = v[2];
+                stamps[1] = v[3];
             }
             return KGPU_OK;
         }
@@ -554,8 +561,37 @@ int kgpu_serve_get_stats(kgpu_ctx* ctx, kgpu_serve_stats* out) {
     return KGPU_OK;
 }
 
-int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
-                      int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns, uint64_t* detail) {
+// Host monotonic time minus the device's %globaltimer, estimated from the
+// dispatcher's heartbeat word (the timer's value, written every 16th idle
+// poll): a load that sees a new value v ended at host time t >= the store's
+// visibility >= v + offset, so t - v bounds the offset from above, and the
+// smallest such bound over about 2 ms of samples is the estimate.  That is
+// the true offset plus the shortest device-to-host store latency, so device
+// times converted with it come out late by that latency (under a
+// microsecond over NVLink-C2C).  (The host time must be taken after the
+// load: one taken before it is no bound if the thread stalls in between.)
+// Needs a running, idle serving kernel; 0 if the word did not move.  *at:
+// the host time the estimate stands for (the middle of the samples).
+static int64_t heartbeat_offset(const ServeState& st, uint64_t* at) {
+    const unsigned long long* hb = &st.hdr->heartbeat;
+    unsigned long long last = load_acquire(hb);
+    int64_t best = INT64_MAX;
+    const uint64_t begin = now_ns(), end = begin + 2000000;
+    for (uint64_t t = begin; t < end;) {
+        const unsigned long long v = load_acquire(hb);
+        t = now_ns();
+        if (v != last) {
+            last = v;
+            best = std::min<int64_t>(best, (int64_t)t - (int64_t)v);
+        }
+    }
+    *at = begin + 1000000;
+    return best == INT64_MAX ? 0 : best;
+}
+
+static int replay_serve_impl(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
+                             int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns, uint64_t* detail,
+                             int64_t* stages, int64_t* offset_out) {
     if (!ctx || !reqs || !arrival_ns || !latency_ns || !n) return KGPU_EINVAL;
     std::vector<ReqDesc> descs(n);
     uint32_t tile_chunks;
@@ -578,6 +614,17 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
         }
     }
     ServeState& st = ctx->serve;
+    // the offset is estimated before and after the run and interpolated per
+    // request, in case the two clocks run at slightly different rates
+    int64_t off0 = 0;
+    uint64_t at0 = 0;
+    if (stages) {
+        {
+            std::lock_guard<std::mutex> lk(ctx->serve_mu);
+            if (st.stopping || ensure_running(ctx, st)) return KGPU_EIO;
+        }
+        off0 = heartbeat_offset(st, &at0);
+    }
     std::unique_ptr<std::atomic<uint64_t>[]> seq_of(new std::atomic<uint64_t>[n]);
     for (size_t i = 0; i < n; i++) {
         seq_of[i].store(UINT64_MAX, std::memory_order_relaxed);
@@ -605,12 +652,19 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
                 const uint32_t slot = (uint32_t)(seq & (nslots - 1));
                 if (load_acquire(&st.done_seq[slot]) >= seq + 1) {
                     latency_ns[i] = t - (t0 + arrival_ns[i]);
-                    if (detail) {  // 0, 0 once the slot has retired a later request too
+                    if (detail || stages) {  // 0s once the slot has retired a later request too
                         int code = 0;
-                        uint64_t a = 0, b = 0;
-                        if (!read_completed(st, seq, &code, &a, &b)) a = b = 0;
-                        detail[3 * i + 1] = a;
-                        detail[3 * i + 2] = b;
+                        uint64_t v[ServeState::kStamps] = {};
+                        if (!read_completed(st, seq, &code, v))
+                            for (auto& x : v) x = 0;
+                        if (detail) {
+                            detail[3 * i + 1] = v[2];
+                            detail[3 * i + 2] = v[3];
+                        }
+                        if (stages) {  // raw device stamps for now, converted after the run
+                            for (int k = 0; k < ServeState::kStamps; k++) stages[kStageWords * i + 1 + k] = (int64_t)v[k];
+                            stages[kStageWords * i + 5] = (int64_t)(t - (t0 + arrival_ns[i]));
+                        }
                     }
                     last_done = t;
                     done++;
@@ -660,6 +714,10 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
             if (j > i) {
                 const int c = commit(ctx, st);
                 if (c) r = c;
+                if (stages) {
+                    const uint64_t tc = st.last_publish_ns;
+                    for (size_t q = i; q < j; q++) stages[kStageWords * q] = (int64_t)(tc - (t0 + arrival_ns[q]));
+                }
             }
         }
         if (j > i) produced.store(j, std::memory_order_release);
@@ -680,9 +738,42 @@ int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* a
             if (latency_ns[i] == UINT64_MAX) rc = KGPU_ETIMEDOUT;
     }
     if (wall_ns) *wall_ns = last_done - t0;
+    if (stages) {
+        // device stamps to nanoseconds since each request's arrival, on the
+        // host clock; a lost stamp (0) becomes INT64_MIN
+        uint64_t at1 = 0;
+        const int64_t off1 = rc ? off0 : heartbeat_offset(st, &at1);
+        if (offset_out) {
+            offset_out[0] = off0;
+            offset_out[1] = off1;
+        }
+        const double slope = at1 > at0 ? (double)(off1 - off0) / (double)(at1 - at0) : 0.0;
+        for (size_t i = 0; i < n; i++) {
+            const int64_t arr = (int64_t)(t0 + arrival_ns[i]);
+            const int64_t off = off0 + (int64_t)(slope * (double)(arr - (int64_t)at0));
+            for (int k = 1; k <= ServeState::kStamps; k++) {
+                int64_t& x = stages[kStageWords * i + k];
+                x = x ? x + off - arr : INT64_MIN;
+            }
+        }
+    }
     std::lock_guard<std::mutex> lk(ctx->serve_mu);
     reap(st);
     return rc;
+}
+
+int kgpu_replay_serve(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
+                      int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns, uint64_t* detail) {
+    return replay_serve_impl(ctx, reqs, arrival_ns, n, timeout_ns, latency_ns, wall_ns, detail, nullptr, nullptr);
+}
+
+int kgpu_replay_serve_stages(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,
+                             int64_t timeout_ns, uint64_t* latency_ns, uint64_t* wall_ns, int64_t* stages,
+                             int64_t* clock_offset_ns) {
+    if (!stages) return KGPU_EINVAL;
+    for (size_t i = 0; i < kStageWords * n; i++) stages[i] = 0;
+    return replay_serve_impl(ctx, reqs, arrival_ns, n, timeout_ns, latency_ns, wall_ns, nullptr, stages,
+                             clock_offset_ns);
 }
 
 int kgpu_replay_launches(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t* arrival_ns, size_t n,

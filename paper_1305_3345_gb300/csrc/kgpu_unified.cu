@@ -234,6 +234,33 @@ __device__ __forceinline__ void tile_cbc_enc(const ReqDesc& d, uint64_t p0, uint
 // (the two-table round of uni_col) and reads its own round-key word from the
 // warp's key slot (the quad's four words share one wavefront).  Lanes without
 // a page step along with predicated-off memory accesses.
+// One block of a four-lane chain: x is this lane's column of the block to
+// encipher (plaintext xor chain value), key the shared address of its column
+// of round 0 (words 4r + col of the schedule).
+template <int NR>
+__device__ __forceinline__ uint32_t quad_encrypt(uint32_t x, uint32_t s1, uint32_t s2, uint32_t s3,
+                                                 const UniLanes& L, uint32_t key) {
+    auto key_word = [&](int r) {
+        uint32_t v;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(key + 16u * (uint32_t)r));
+        return v;
+    };
+    x ^= key_word(0);
+#pragma unroll
+    for (int r = 1; r < NR; r++) {
+        const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
+        const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
+        const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
+        x = uni_col(x, a1, a2, a3, key_word(r), L);
+    }
+    const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
+    const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
+    const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
+#define KGPU_FIN(P, v) lds_tab<kSmemBase>(row_addr<P>(v, L.f))
+    return merge_bytes(KGPU_FIN(0, x), KGPU_FIN(1, a1), KGPU_FIN(2, a2), KGPU_FIN(3, a3)) ^ key_word(14);
+#undef KGPU_FIN
+}
+
 template <int NR>
 __device__ __forceinline__ void quad_chains(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
     const uint32_t lane = lane_id();
@@ -245,11 +272,6 @@ __device__ __forceinline__ void quad_chains(const ReqDesc& d, uint64_t p0, uint6
     const uint32_t* in = reinterpret_cast<const uint32_t*>(d.src + (valid ? page : p0) * bpp) + c;
     uint32_t* out = reinterpret_cast<uint32_t*>(d.dst + (valid ? page : p0) * bpp) + c;
     const uint32_t key = K.data_saddr + 4u * c;  // word 4r + c of the schedule: round r, this column
-    auto key_word = [&](int r) {
-        uint32_t v;
-        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(key + 16u * (uint32_t)r));
-        return v;
-    };
     const uint32_t s1 = base | ((c + 1) & 3u), s2 = base | ((c + 2) & 3u), s3 = base | ((c + 3) & 3u);
     uint32_t x = valid ? reinterpret_cast<const uint32_t*>(d.ivs + page)[c] : 0u;
     // the chain is sequential, so plaintext is fetched four blocks ahead
@@ -263,21 +285,63 @@ __device__ __forceinline__ void quad_chains(const ReqDesc& d, uint64_t p0, uint6
         q1 = q2;
         q2 = q3;
         if (valid && i + 4 < bpp) q3 = in[4 * (i + 4)];
-        x ^= cur ^ key_word(0);
-#pragma unroll
-        for (int r = 1; r < NR; r++) {
-            const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
-            const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
-            const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
-            x = uni_col(x, a1, a2, a3, key_word(r), L);
-        }
-        const uint32_t a1 = __shfl_sync(0xffffffffu, x, s1);
-        const uint32_t a2 = __shfl_sync(0xffffffffu, x, s2);
-        const uint32_t a3 = __shfl_sync(0xffffffffu, x, s3);
-#define KGPU_FIN(P, v) lds_tab<kSmemBase>(row_addr<P>(v, L.f))
-        x = merge_bytes(KGPU_FIN(0, x), KGPU_FIN(1, a1), KGPU_FIN(2, a2), KGPU_FIN(3, a3)) ^ key_word(14);
-#undef KGPU_FIN
+        x = quad_encrypt<NR>(x ^ cur, s1, s2, s3, L, key);
         if (valid) out[4 * i] = x;
+    }
+}
+
+// Four-lane chains over pages in registered host memory: the warp moves 8
+// blocks (one 128-byte line) of each of its 8 pages at a time between the
+// buffers and its scratch area with whole-line accesses -- a four-lane load
+// straight from the pages would move a whole line over the link for 16
+// useful bytes -- and the quads run their chains on the scratch copy.  The
+// next chunk's lines are loaded from the host while the current chunk is
+// enciphered.  Scratch: two 1-KiB halves, [page of the tile][block of the
+// chunk]; pages must hold a multiple of 8 blocks.  __syncwarp orders the
+// lanes' scratch accesses.
+template <int NR>
+__device__ __forceinline__ void quad_chains_staged(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K,
+                                                   uint4* stage) {
+    const uint32_t lane = lane_id();
+    const uint32_t c = lane & 3u, base = lane & ~3u, qp = lane >> 2;
+    const UniLanes L = uni_lanes(lane, 0);
+    const bool valid = p0 + qp < p1;
+    const uint32_t bpp = d.unit_blocks;
+    const uint32_t key = K.data_saddr + 4u * c;
+    const uint32_t s1 = base | ((c + 1) & 3u), s2 = base | ((c + 2) & 3u), s3 = base | ((c + 3) & 3u);
+    uint32_t x = valid ? reinterpret_cast<const uint32_t*>(d.ivs + p0 + qp)[c] : 0u;
+    // copy positions: lanes 8p..8p+7 move page p's line (pages 0-3, then 4-7)
+    const uint32_t cp_blk = lane & 7u, cp_pg0 = lane >> 3, cp_pg1 = cp_pg0 + 4;
+    const bool ok0 = p0 + cp_pg0 < p1, ok1 = p0 + cp_pg1 < p1;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    auto fetch = [&](uint32_t chunk, uint4& v0, uint4& v1) {
+        v0 = ok0 ? d.src[(p0 + cp_pg0) * bpp + chunk + cp_blk] : z;
+        v1 = ok1 ? d.src[(p0 + cp_pg1) * bpp + chunk + cp_blk] : z;
+    };
+    uint4 n0, n1;
+    fetch(0, n0, n1);
+    for (uint32_t ch = 0, half = 0; ch < bpp; ch += kStageBlocks, half ^= 64u) {
+        uint4* buf = stage + half;
+        buf[cp_pg0 * kStageBlocks + cp_blk] = n0;
+        buf[cp_pg1 * kStageBlocks + cp_blk] = n1;
+        __syncwarp();
+        if (ch + kStageBlocks < bpp) fetch(ch + kStageBlocks, n0, n1);  // in flight meanwhile
+        // this lane's column of its page's blocks, two blocks ahead (the
+        // scratch copy is near: L1/L2)
+        uint32_t* col = reinterpret_cast<uint32_t*>(buf + qp * kStageBlocks) + c;
+        uint32_t q0 = col[0], q1 = col[4];
+#pragma unroll 1
+        for (uint32_t i = 0; i < kStageBlocks; i++) {
+            const uint32_t cur = q0;
+            q0 = q1;
+            if (i + 2 < kStageBlocks) q1 = col[4 * (i + 2)];
+            x = quad_encrypt<NR>(x ^ cur, s1, s2, s3, L, key);
+            col[4 * i] = x;
+        }
+        __syncwarp();
+        const uint4 o0 = buf[cp_pg0 * kStageBlocks + cp_blk], o1 = buf[cp_pg1 * kStageBlocks + cp_blk];
+        if (ok0) d.dst[(p0 + cp_pg0) * bpp + ch + cp_blk] = o0;
+        if (ok1) d.dst[(p0 + cp_pg1) * bpp + ch + cp_blk] = o1;
     }
 }
 
@@ -289,6 +353,16 @@ __device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0,
         case 10: quad_chains<10>(d, p0, p1, K); break;
         case 12: quad_chains<12>(d, p0, p1, K); break;
         default: quad_chains<14>(d, p0, p1, K); break;
+    }
+}
+
+__device__ __forceinline__ void tile_cbc_enc_quad_staged(const ReqDesc& d, uint64_t p0, uint64_t p1,
+                                                         const WarpKeys& K, uint4* stage) {
+    __syncwarp();
+    switch (K.nr) {
+        case 10: quad_chains_staged<10>(d, p0, p1, K, stage); break;
+        case 12: quad_chains_staged<12>(d, p0, p1, K, stage); break;
+        default: quad_chains_staged<14>(d, p0, p1, K, stage); break;
     }
 }
 
@@ -412,9 +486,10 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
         case KGPU_MODE_ECB: tile_blocks<false>(d, u0, u1, dir, K); break;
         case KGPU_MODE_CBC_DEC: tile_cbc_dec(d, u0, u1, K); break;
         case KGPU_MODE_CBC_ENC:
-            if (stage && (d.flags & (kDescSrcHost | kDescDstHost)) && d.unit_blocks % kStageBlocks == 0)
-                tile_cbc_enc_staged(d, u0, u1, K, stage);
-            else if (QUAD && (d.flags & kDescQuad))
+            if (stage && (d.flags & (kDescSrcHost | kDescDstHost)) && d.unit_blocks % kStageBlocks == 0) {
+                if (QUAD && (d.flags & kDescQuad)) tile_cbc_enc_quad_staged(d, u0, u1, K, stage);
+                else tile_cbc_enc_staged(d, u0, u1, K, stage);
+            } else if (QUAD && (d.flags & kDescQuad))
                 tile_cbc_enc_quad(d, u0, u1, K);
             else
                 tile_cbc_enc(d, u0, u1, K);
@@ -542,7 +617,7 @@ __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
     unsigned long long m = ld_vol(&a.dev->mirrored);   // requests enumerated so far
     unsigned long long pub = ld_vol(&a.dev->tile_head);
     unsigned long long idle_since = t0;
-    unsigned int backoff = 64, reason = 0;
+    unsigned int backoff = 64, reason = 0, idle_polls = 0;
     const unsigned long long ring = a.tile_mask + 1;
     for (;;) {
         unsigned long long h = 0, now = 0;
@@ -561,21 +636,27 @@ __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
         }
         if (m < h) {
             // copy up to 32 new descriptors to device memory, one per lane
+            // (the loads over the host link and the finished-tile count are
+            // issued together: the request's own latency waits on them)
             const unsigned cnt = (unsigned)(h - m < 32 ? h - m : 32);
+            const unsigned long long done_tiles = ld_vol(&a.dev->tile_done);
             unsigned long long nt = 0;
             if (lane < cnt) {
                 const uint32_t s = (uint32_t)((m + lane) & a.slot_mask);
                 const uint4* from = reinterpret_cast<const uint4*>(&a.slots[s]);
                 uint4* to = reinterpret_cast<uint4*>(&a.dslots[s]);
+                uint4 v[5];
 #pragma unroll
-                for (int q = 0; q < 5; q++) to[q] = from[q];  // ReqDesc, ntiles, seq
-                nt = a.dslots[s].ntiles;
+                for (int q = 0; q < 5; q++) v[q] = from[q];  // ReqDesc, ntiles, seq
+#pragma unroll
+                for (int q = 0; q < 5; q++) to[q] = v[q];
+                nt = (unsigned long long)v[4].y << 32 | v[4].x;  // ntiles
+                a.dslots[s].t_disp = now;
                 a.fin[s] = 0;
             }
             // enumerate their tiles, in order, as long as the ring has room;
             // each entry carries the high bits of its position as a tag
             unsigned taken = 0;
-            const unsigned long long done_tiles = ld_vol(&a.dev->tile_done);
             for (unsigned i = 0; i < cnt; i++) {
                 const unsigned long long n_i = __shfl_sync(0xffffffffu, nt, i);
                 if (pub + n_i - done_tiles > ring) break;
@@ -588,6 +669,7 @@ __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
                 pub += n_i;
                 taken++;
             }
+            if (lane < taken) a.dslots[(m + lane) & a.slot_mask].t_pub = gtimer();
             __syncwarp();
             __threadfence();
             if (taken && lane == 0) {
@@ -616,9 +698,12 @@ __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
             reason = kServeExitLifetime;
             break;
         }
-        if (lane == 0) a.hh->heartbeat = now;
+        // the heartbeat (the host's clock-offset reference) every 16th idle
+        // poll: a store over the link just before new work would make that
+        // work's fence wait for it
+        if (lane == 0 && (++idle_polls & 15) == 0) a.hh->heartbeat = now;
         __nanosleep(backoff);
-        if (backoff < 256) backoff <<= 1;
+        if (backoff < 128) backoff <<= 1;
     }
     if (lane == 0) {
         st_release_gpu32(&a.dev->stop, reason);
@@ -673,24 +758,26 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         unsigned long long T = 0;
         if (lane == 0) T = atomicAdd(&a.dev->tile_next, 1ull);
         T = __shfl_sync(0xffffffffu, T, 0);
-        // wait until position T is published (bounded: stop bit, own limit)
+        // wait until position T is published (bounded: stop bit, own limit).
+        // The mailbox holds the published count: the dispatcher writes it
+        // after a fence that follows its tile-ring and descriptor writes, and
+        // the acquire load here orders this warp's reads of them after it.
         int go = 0;
         unsigned int backoff = 32;
         const unsigned long long w0 = gtimer();
         const unsigned long long* box = &a.mbox[blockIdx.x * kMboxStride];
         for (;;) {
             // every lane reads the same word of this CTA's mailbox line
-            const unsigned long long v = __shfl_sync(0xffffffffu, ld_vol(box), 0);
-            const bool published = T < (v & ~kMboxStop);
-            if (published || (v & kMboxStop)) {
-                go = T < ld_acquire_gpu(&a.dev->tile_head) ? 1 : 0;
-                go = __shfl_sync(0xffffffffu, go, 0);
-                if (go || (v & kMboxStop)) break;
+            const unsigned long long v = __shfl_sync(0xffffffffu, ld_acquire_gpu(box), 0);
+            if (T < (v & ~kMboxStop)) {
+                go = 1;
+                break;
             }
+            if (v & kMboxStop) break;
             const unsigned long long now = __shfl_sync(0xffffffffu, gtimer(), 0);
             if (now - w0 > own_idle) break;
             __nanosleep(backoff);
-            if (backoff < 1024) backoff <<= 1;
+            if (backoff < 256) backoff <<= 1;
         }
         if (!go) break;
 
@@ -731,6 +818,8 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
             const unsigned long long t_end = __shfl_sync(0xffffffffu, gtimer(), 0);
             if (lane == 0) {
                 a.t_done[s] = t_end;
+                a.t_disp[s] = a.dslots[s].t_disp;
+                a.t_pub[s] = a.dslots[s].t_pub;
                 st_release_sys(&a.done_seq[s], seq + 1);
                 atomicAdd(&a.dev->done_count, 1ull);
             }

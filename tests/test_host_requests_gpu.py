@@ -276,3 +276,45 @@ def test_cbc_encrypt_of_host_pages(ctx, threads, page, npages):
         for b in (src, dst, ivs):
             ctx.host_unregister(b)
         ctx.delkey(kh)
+
+
+@pytest.mark.parametrize("bits", [128, 192, 256])
+@pytest.mark.parametrize("page,npages", [(4096, 45), (512, 1025), (128, 31), (4112, 33), (1024, 9)])
+def test_cbc_encrypt_of_host_pages_through_the_ring(ctx, bits, page, npages):
+    """CBC encryption of host pages through the serving ring while it keeps up:
+    pages of a multiple of 8 blocks run four lanes to a page through the
+    warp's scratch (8 pages a tile, whole-line copies, the next chunk fetched
+    while the current one is enciphered), the others one lane per page; one
+    request alone, then the same request in place."""
+    import torch
+    import paper_1305_3345_gb300 as kg
+    seed = 900 + page + npages + bits
+    data = w.seeded_bytes(seed, w.STREAM_DATA, page * npages)
+    ivs_np = w.page_ivs(seed, npages)
+    key = w.single_key(seed, bits)
+    src, dst = pinned(data.size), pinned(data.size)
+    src.copy_(torch.from_numpy(data))
+    ivs = pinned(ivs_np.size)
+    ivs.copy_(torch.from_numpy(ivs_np.reshape(-1).copy()))
+    kh = ctx.setkey(key, False)
+    for b in (src, dst, ivs):
+        ctx.host_register(b)
+    ref = oracle.cbc(key, 0, data, page, ivs_np)
+    try:
+        ctx.serve_start()
+        try:
+            for out in (dst, src):
+                r = np.zeros(1, dtype=kg.request_dtype())
+                r["mode"], r["key"] = w.MODE_CBC_ENC, kh
+                r["src"], r["dst"], r["ivs"] = src.data_ptr(), out.data_ptr(), ivs.data_ptr()
+                r["len"], r["unit_size"] = data.size, page
+                r["flags"] = kg.REQ_SRC_HOST | kg.REQ_DST_HOST | kg.REQ_IVS_HOST
+                rc, st, _ = ctx.serve_poll(ctx.serve_submit(r[0]), 10_000_000_000)
+                assert rc == 0 and st == 0
+                assert np.array_equal(out.numpy(), ref)
+        finally:
+            assert ctx.serve_stop(5_000_000_000) == 0
+    finally:
+        for b in (src, dst, ivs):
+            ctx.host_unregister(b)
+        ctx.delkey(kh)
