@@ -417,11 +417,17 @@ int kgpu_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* req_st
     if (timeout_ns < 0) {
         e = cudaEventSynchronize(ev);
     } else {
-        auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns);
+        // spin for the first 200 us (a short batch is done well within it,
+        // and a sleep costs tens of microseconds of timer slack), then sleep
+        // between checks
+        const auto start = std::chrono::steady_clock::now();
+        const auto deadline = start + std::chrono::nanoseconds(timeout_ns);
         for (;;) {
             e = cudaEventQuery(ev);
-            if (e != cudaErrorNotReady || std::chrono::steady_clock::now() >= deadline) break;
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            const auto now = std::chrono::steady_clock::now();
+            if (e != cudaErrorNotReady || now >= deadline) break;
+            if (now - start > std::chrono::microseconds(200))
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
     }
     std::lock_guard<std::mutex> lk(ctx->batch_mu);
