@@ -317,7 +317,7 @@ def serving_summary(sv, svh, rt, es=None):
     if sv.get("ring_capacity"):
         out["ring_capacity_GB/s"] = _r(sv["ring_capacity"]["ring"]["GB/s"])
     out["roundtrip_4k_p50_p99_us"] = {k: [_r((rt[k]["latency"] or {}).get("p50_us")), p99(rt[k])]
-                                      for k in ("ring", "launch", "host_ring", "host_launch")}
+                                      for k in ("ring", "launch")}
     if es:
         out["empty_4k_host_p50_us_512_1024_2048"] = {
             form: [_r(es["host"][t][form]["p50_us"]) for t in ("512", "1024", "2048")] for form in ("ring", "launch")}
@@ -972,7 +972,7 @@ def run_kgpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": (WORKLOAD if nbytes == GIB else f"AES-256-XTS encrypt, {nbytes} B (profiling case)")
                    + (" -- bitsliced comparison variant" if bitsliced else ""),
-                   "bytes_per_gpu": nbytes, "l2": "inputs larger than L2 (1 GiB vs 129 MB)",
+                   "bytes_per_gpu": nbytes, "l2": "inputs > L2 (1 GiB vs 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "roofline_hbm": roofline_hbm, "clocks": clocks,
         "gpu_launches": args.steps * (2 if bitsliced else 1),  # bitsliced: tweak pre-pass + cipher
@@ -1062,7 +1062,7 @@ def run_kgpu(args):
             ctx.host_unregister(hdst)
         line["e2e"] = {"value": world * GIB / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": world * GIB,
                        "d2h_bytes_per_step": world * GIB, "steps": e2e_steps, "statistic": "median step",
-                       "call": "kgpu_aes_xts_crypt_host, registered pinned pages"}
+                       "call": "kgpu_aes_xts_crypt_host"}
         dt, dmean = host_steps()
         e2e_forms = {}
         e2e_forms["e2e_copy_pipeline"] = {"value": world * GIB / dt / 1e9, "unit": "GB/s",

@@ -377,14 +377,20 @@ int kgpu_poll_each(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* r
         else pending.push_back(i);
     }
     int rc = KGPU_OK;
+    std::vector<uint32_t> found;
+    found.reserve(n);
     while (!pending.empty()) {
-        const uint64_t t = now();
         size_t keep = 0;
+        found.clear();
         for (uint32_t i : pending) {
             const unsigned long long v = __atomic_load_n(&words[i], __ATOMIC_ACQUIRE);
-            if ((uint32_t)(v >> 32) == tag) done_ns[i] = t;
+            if ((uint32_t)(v >> 32) == tag) found.push_back(i);
             else pending[keep++] = i;
         }
+        // completions are stamped with the time after the scan that saw them:
+        // late by at most the scan, never early
+        const uint64_t t = now();
+        for (uint32_t i : found) done_ns[i] = t;
         pending.resize(keep);
         if (!pending.empty() && t >= deadline) {
             rc = KGPU_ETIMEDOUT;

@@ -651,7 +651,11 @@ static int replay_serve_impl(kgpu_ctx* ctx, const kgpu_request* reqs, const uint
                 const uint64_t seq = seq_of[i].load(std::memory_order_acquire);
                 const uint32_t slot = (uint32_t)(seq & (nslots - 1));
                 if (load_acquire(&st.done_seq[slot]) >= seq + 1) {
-                    latency_ns[i] = t - (t0 + arrival_ns[i]);
+                    // the time after the completion was seen: one taken at the
+                    // start of the scan would read early if the thread
+                    // stalled during it
+                    const uint64_t tc = now_ns();
+                    latency_ns[i] = tc - (t0 + arrival_ns[i]);
                     if (detail || stages) {  // 0s once the slot has retired a later request too
                         int code = 0;
                         uint64_t v[ServeState::kStamps] = {};
@@ -663,10 +667,10 @@ static int replay_serve_impl(kgpu_ctx* ctx, const kgpu_request* reqs, const uint
                         }
                         if (stages) {  // raw device stamps for now, converted after the run
                             for (int k = 0; k < ServeState::kStamps; k++) stages[kStageWords * i + 1 + k] = (int64_t)v[k];
-                            stages[kStageWords * i + 5] = (int64_t)(t - (t0 + arrival_ns[i]));
+                            stages[kStageWords * i + 5] = (int64_t)(tc - (t0 + arrival_ns[i]));
                         }
                     }
-                    last_done = t;
+                    last_done = std::max(last_done, tc);
                     done++;
                 } else {
                     pending[w++] = i;

@@ -148,6 +148,215 @@ __device__ __forceinline__ void tile_blocks(const ReqDesc& d, uint64_t c0, uint6
     }
 }
 
+// Two blocks per lane through the unified cipher at once (u-frame state and
+// key): one round-key broadcast serves both, and the warp keeps twice the
+// independent lookups in flight.  Used by the 512-thread batch kernel, which
+// has the registers for it.
+__device__ __forceinline__ void cipher_u2(uint32_t& a0, uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& b0,
+                                          uint32_t& b1, uint32_t& b2, uint32_t& b3, uint32_t key_saddr, int nr,
+                                          const UniLanes& L) {
+    uint4 k = round_key(key_saddr, 0);
+    a0 ^= k.x, a1 ^= k.y, a2 ^= k.z, a3 ^= k.w;
+    b0 ^= k.x, b1 ^= k.y, b2 ^= k.z, b3 ^= k.w;
+#pragma unroll 1
+    for (int r = 1; r < nr; r++) {
+        k = round_key(key_saddr, r);
+        const uint32_t s0 = uni_col(a0, a1, a2, a3, k.x, L), u0 = uni_col(b0, b1, b2, b3, k.x, L);
+        const uint32_t s1 = uni_col(a1, a2, a3, a0, k.y, L), u1 = uni_col(b1, b2, b3, b0, k.y, L);
+        const uint32_t s2 = uni_col(a2, a3, a0, a1, k.z, L), u2 = uni_col(b2, b3, b0, b1, k.z, L);
+        const uint32_t s3 = uni_col(a3, a0, a1, a2, k.w, L), u3 = uni_col(b3, b0, b1, b2, k.w, L);
+        a0 = s0, a1 = s1, a2 = s2, a3 = s3;
+        b0 = u0, b1 = u1, b2 = u2, b3 = u3;
+    }
+    k = round_key(key_saddr, 14);  // the final round key sits in words 56..59
+#define KGPU_FIN(P, x) lds_tab<kSmemBase>(row_addr<P>(x, L.f))
+    const uint32_t o0 = merge_bytes(KGPU_FIN(0, a0), KGPU_FIN(1, a1), KGPU_FIN(2, a2), KGPU_FIN(3, a3)) ^ k.x;
+    const uint32_t q0 = merge_bytes(KGPU_FIN(0, b0), KGPU_FIN(1, b1), KGPU_FIN(2, b2), KGPU_FIN(3, b3)) ^ k.x;
+    const uint32_t o1 = merge_bytes(KGPU_FIN(0, a1), KGPU_FIN(1, a2), KGPU_FIN(2, a3), KGPU_FIN(3, a0)) ^ k.y;
+    const uint32_t q1 = merge_bytes(KGPU_FIN(0, b1), KGPU_FIN(1, b2), KGPU_FIN(2, b3), KGPU_FIN(3, b0)) ^ k.y;
+    const uint32_t o2 = merge_bytes(KGPU_FIN(0, a2), KGPU_FIN(1, a3), KGPU_FIN(2, a0), KGPU_FIN(3, a1)) ^ k.z;
+    const uint32_t q2 = merge_bytes(KGPU_FIN(0, b2), KGPU_FIN(1, b3), KGPU_FIN(2, b0), KGPU_FIN(3, b1)) ^ k.z;
+    const uint32_t o3 = merge_bytes(KGPU_FIN(0, a3), KGPU_FIN(1, a0), KGPU_FIN(2, a1), KGPU_FIN(3, a2)) ^ k.w;
+    const uint32_t q3 = merge_bytes(KGPU_FIN(0, b3), KGPU_FIN(1, b0), KGPU_FIN(2, b1), KGPU_FIN(3, b2)) ^ k.w;
+#undef KGPU_FIN
+    a0 = o0, a1 = o1, a2 = o2, a3 = o3;
+    b0 = q0, b1 = q1, b2 = q2, b3 = q3;
+}
+
+// Two blocks in natural column order in direction dir (see cipher_block).
+__device__ __forceinline__ void cipher_block2(uint4& a, uint4& b, uint32_t key_saddr, int nr, const UniLanes& L,
+                                              int dir) {
+    if (dir) {
+        uint32_t t = a.y;
+        a.y = a.w, a.w = t;
+        t = b.y;
+        b.y = b.w, b.w = t;
+    }
+    cipher_u2(a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, key_saddr, nr, L);
+    if (dir) {
+        uint32_t t = a.y;
+        a.y = a.w, a.w = t;
+        t = b.y;
+        b.y = b.w, b.w = t;
+    }
+}
+
+// tile_blocks with two 32-block chunks per step: a lane takes block b of
+// chunk c and block b of chunk c + 1, whose tweak is the same lane's tweak
+// moved on by one chunk.
+template <bool TWEAK>
+__device__ __forceinline__ void tile_blocks2(const ReqDesc& d, uint64_t c0, uint64_t c1, int dir,
+                                             const WarpKeys& K) {
+    __syncwarp();
+    const uint32_t lane = lane_id();
+    const UniLanes L = uni_lanes(lane, dir);
+    const UniLanes LE = uni_lanes(lane, 0);
+    uint64_t blk = (c0 << 5) + lane;
+    const uint32_t bps = d.unit_blocks;
+    uint64_t base = 0;
+    uint32_t srel = 0, j = 0;
+    uint32_t z0 = 0, z1 = 0, z2 = 0, z3 = 0, t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+
+    auto tweak_batch = [&]() {
+        uint64_t unit = d.first_sector + base + lane;
+        z0 = (uint32_t)unit;
+        z1 = (uint32_t)(unit >> 32);
+        z2 = 0;
+        z3 = 0;
+        cipher_u(z0, z1, z2, z3, K.twk_saddr, K.nr, LE);
+    };
+    // the lane's block and tweak moved on by one chunk (every lane together:
+    // the tweak batch and the shuffles are warp-wide)
+    auto advance = [&]() {
+        blk += 32;
+        if (!TWEAK) return;
+        j += 32;
+        bool crossed = false;
+        if (j >= bps) {
+            uint32_t ns = j / bps;
+            srel += ns;
+            j -= ns * bps;
+            crossed = true;
+        }
+        if (__any_sync(0xffffffffu, srel >= 32)) {
+            uint32_t adv = __shfl_sync(0xffffffffu, srel, 0);
+            base += adv;
+            srel -= adv;
+            tweak_batch();
+        }
+        if (__any_sync(0xffffffffu, crossed)) {
+            uint32_t u0 = __shfl_sync(0xffffffffu, z0, srel & 31);
+            uint32_t u1 = __shfl_sync(0xffffffffu, z1, srel & 31);
+            uint32_t u2 = __shfl_sync(0xffffffffu, z2, srel & 31);
+            uint32_t u3 = __shfl_sync(0xffffffffu, z3, srel & 31);
+            if (crossed) {
+                t0 = u0;
+                t1 = u1;
+                t2 = u2;
+                t3 = u3;
+                gf128_mul_xk(t0, t1, t2, t3, j);
+            }
+        }
+        if (!crossed) gf128_mul_x32(t0, t1, t2, t3);
+    };
+    if (TWEAK) {
+        base = (c0 << 5) / bps;
+        uint64_t sabs = blk / bps;
+        srel = (uint32_t)(sabs - base);
+        j = (uint32_t)(blk - sabs * bps);
+        tweak_batch();
+        t0 = __shfl_sync(0xffffffffu, z0, srel);
+        t1 = __shfl_sync(0xffffffffu, z1, srel);
+        t2 = __shfl_sync(0xffffffffu, z2, srel);
+        t3 = __shfl_sync(0xffffffffu, z3, srel);
+        gf128_mul_xpow(t0, t1, t2, t3, j);
+    }
+    const uint4 zz = make_uint4(0, 0, 0, 0);
+    // the next step's two chunks are fetched while this step's are enciphered
+    uint4 na = (c0 < c1 && blk < d.nblocks) ? d.src[blk] : zz;
+    uint4 nb = (c0 + 1 < c1 && blk + 32 < d.nblocks) ? d.src[blk + 32] : zz;
+    for (uint64_t c = c0; c < c1; c += 2) {
+        const bool two = c + 1 < c1;
+        uint4 va = na, vb = nb;
+        const uint64_t ba = blk;
+        const uint32_t a0 = t0, a1 = t1, a2 = t2, a3 = t3;
+        if (two) advance();
+        if (c + 2 < c1 && ba + 64 < d.nblocks) na = d.src[ba + 64];
+        if (c + 3 < c1 && ba + 96 < d.nblocks) nb = d.src[ba + 96];
+        if (TWEAK) {
+            xor4(va, a0, a1, a2, a3);
+            xor4(vb, t0, t1, t2, t3);
+        }
+        cipher_block2(va, vb, K.data_saddr, K.nr, L, dir);
+        if (TWEAK) {
+            xor4(va, a0, a1, a2, a3);
+            xor4(vb, t0, t1, t2, t3);
+        }
+        if (ba < d.nblocks) d.dst[ba] = va;
+        if (two && ba + 32 < d.nblocks) d.dst[ba + 32] = vb;
+        if (c + 2 < c1) advance();
+    }
+}
+
+// tile_cbc_dec with two 32-block steps at once: a lane takes block b of this
+// step's first half and block b of its second half.
+__device__ __forceinline__ void tile_cbc_dec2(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
+    __syncwarp();
+    const uint32_t lane = lane_id();
+    const UniLanes L = uni_lanes(lane, 1);
+    const uint32_t bpp = d.unit_blocks;
+    const uint64_t bend = p1 * bpp;
+    uint64_t blk = p0 * bpp + lane;
+    uint64_t pa = p0 + lane / bpp, pb = p0 + (lane + 32) / bpp;
+    uint32_t ja = lane % bpp, jb = (lane + 32) % bpp;
+    auto step = [&](uint64_t& page, uint32_t& j) {
+        j += 64;
+        if (j >= bpp) {
+            uint32_t ns = j / bpp;
+            page += ns;
+            j -= ns * bpp;
+        }
+    };
+    uint4 carry = make_uint4(0, 0, 0, 0);
+    const uint4 zz = make_uint4(0, 0, 0, 0);
+    uint4 na = blk < bend ? d.src[blk] : zz;
+    uint4 nb = blk + 32 < bend ? d.src[blk + 32] : zz;
+    const uint32_t src_lane = (lane + 31) & 31;
+    for (uint64_t b = p0 * bpp; b < bend; b += 64) {
+        const uint4 ca = na, cb = nb;
+        if (blk + 64 < bend) na = d.src[blk + 64];  // prefetch the next step
+        if (blk + 96 < bend) nb = d.src[blk + 96];
+        // lane i takes lane i-1's block in each half; lane 0 of the second
+        // half takes lane 31 of the first, lane 0 of the first the last step's
+        uint4 xa, xb;
+        xa.x = __shfl_sync(0xffffffffu, ca.x, src_lane);
+        xa.y = __shfl_sync(0xffffffffu, ca.y, src_lane);
+        xa.z = __shfl_sync(0xffffffffu, ca.z, src_lane);
+        xa.w = __shfl_sync(0xffffffffu, ca.w, src_lane);
+        xb.x = __shfl_sync(0xffffffffu, cb.x, src_lane);
+        xb.y = __shfl_sync(0xffffffffu, cb.y, src_lane);
+        xb.z = __shfl_sync(0xffffffffu, cb.z, src_lane);
+        xb.w = __shfl_sync(0xffffffffu, cb.w, src_lane);
+        uint4 prev_a = xa, prev_b = xb;
+        if (lane == 0) {
+            prev_a = carry;
+            prev_b = xa;  // lane 31 of the first half
+            carry = xb;   // lane 31 of the second half
+        }
+        if (blk < bend && ja == 0) prev_a = d.ivs[pa];
+        if (blk + 32 < bend && jb == 0) prev_b = d.ivs[pb];
+        uint4 va = ca, vb = cb;
+        cipher_block2(va, vb, K.data_saddr, K.nr, L, 1);
+        xor4(va, prev_a.x, prev_a.y, prev_a.z, prev_a.w);
+        xor4(vb, prev_b.x, prev_b.y, prev_b.z, prev_b.w);
+        if (blk < bend) d.dst[blk] = va;
+        if (blk + 32 < bend) d.dst[blk + 32] = vb;
+        blk += 64;
+        step(pa, ja);
+        step(pb, jb);
+    }
+}
+
 // CBC decryption of pages [p0, p1) of one request (see cbc_dec_kernel).
 __device__ __forceinline__ void tile_cbc_dec(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K) {
     __syncwarp();
@@ -440,7 +649,9 @@ __device__ __forceinline__ uint32_t find_request(const uint64_t* tile_start, uin
 // Runs one tile of request d; returns 0 or a KGPU_E* status for the request.
 // stage: this warp's scratch area, or null.  QUAD: compile the four-lanes-per-
 // page CBC encryption in (only the serving kernel's descriptors ask for it,
-// and it would cost the batch kernels registers).
+// and it would cost the batch kernels registers).  TWO: XTS, ECB and CBC
+// decryption two blocks per lane at a time (the 512-thread batch kernel,
+// where throughput counts and the registers are there).
 // The empty service (KGPU_MODE_COPY): units [u0, u1) of unit_blocks blocks
 // each are copied through unchanged, one 16-byte access per lane per step.
 __device__ __forceinline__ void tile_copy(const ReqDesc& d, uint64_t u0, uint64_t u1) {
@@ -448,7 +659,7 @@ __device__ __forceinline__ void tile_copy(const ReqDesc& d, uint64_t u0, uint64_
     for (uint64_t b = u0 * d.unit_blocks + lane_id(); b < b1; b += 32) d.dst[b] = d.src[b];
 }
 
-template <bool QUAD>
+template <bool QUAD, bool TWO = false>
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
                                      WarpKeys& K, uint32_t& cur_sel, uint4* stage) {
     const uint32_t lane = lane_id();
@@ -482,9 +693,18 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
     uint64_t u1 = u0 + d.tile_units;
     if (u1 > units) u1 = units;
     switch (d.mode) {
-        case KGPU_MODE_XTS: tile_blocks<true>(d, u0, u1, dir, K); break;
-        case KGPU_MODE_ECB: tile_blocks<false>(d, u0, u1, dir, K); break;
-        case KGPU_MODE_CBC_DEC: tile_cbc_dec(d, u0, u1, K); break;
+        case KGPU_MODE_XTS:
+            if (TWO) tile_blocks2<true>(d, u0, u1, dir, K);
+            else tile_blocks<true>(d, u0, u1, dir, K);
+            break;
+        case KGPU_MODE_ECB:
+            if (TWO) tile_blocks2<false>(d, u0, u1, dir, K);
+            else tile_blocks<false>(d, u0, u1, dir, K);
+            break;
+        case KGPU_MODE_CBC_DEC:
+            if (TWO) tile_cbc_dec2(d, u0, u1, K);
+            else tile_cbc_dec(d, u0, u1, K);
+            break;
         case KGPU_MODE_CBC_ENC:
             if (stage && (d.flags & (kDescSrcHost | kDescDstHost)) && d.unit_blocks % kStageBlocks == 0) {
                 if (QUAD && (d.flags & kDescQuad)) tile_cbc_enc_quad_staged(d, u0, u1, K, stage);
@@ -569,7 +789,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
         const uint32_t k = find_request(tile_start, nreq, t);
         const uint32_t i = order[k];
         const ReqDesc d = reqs[i];
-        const int st = run_tile<false>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile<false, (THREADS <= 512)>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
         if (st && lane == 0) a.status[i] = st;
         if (a.fin) {
             // per-request completion: the warp that finishes a request's last
@@ -700,8 +920,10 @@ __device__ void serve_dispatcher(const ServeArgs& a, unsigned long long t0) {
         }
         // the heartbeat (the host's clock-offset reference) every 16th idle
         // poll: a store over the link just before new work would make that
-        // work's fence wait for it
-        if (lane == 0 && (++idle_polls & 15) == 0) a.hh->heartbeat = now;
+        // work's fence wait for it.  A system-scope release, so that it is
+        // sent on at once (a plain store may wait in the cache, and the host
+        // would then bound the offset too high).
+        if (lane == 0 && (++idle_polls & 15) == 0) st_release_sys(&a.hh->heartbeat, now);
         __nanosleep(backoff);
         if (backoff < 128) backoff <<= 1;
     }
