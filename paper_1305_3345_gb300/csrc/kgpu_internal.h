@@ -201,5 +201,14 @@ cudaError_t configure_batch_kernels();  // unified kernels: opt-in to large dyna
 // Unified-kernel shared memory: three table regions plus one 512-B key slot
 // per warp (data schedule, then the XTS tweak schedule, 240 B each).
 inline size_t unified_smem_bytes(int threads) { return 3 * kRegionBytes + (size_t)(threads / 32) * 512; }
+// The serving kernel adds, after the key slots, a staging area per warp for
+// four-lane CBC encryption of host pages: 8 pages x 8 blocks, rows padded to
+// 144 bytes so that both the whole-line copies and the column reads are free
+// of bank conflicts.
+constexpr size_t kServeStageRow = 144;
+constexpr size_t kServeStageWarpBytes = 8 * kServeStageRow;
+inline size_t serve_smem_bytes() {
+    return unified_smem_bytes(kServeThreads) + (size_t)(kServeThreads / 32) * kServeStageWarpBytes;
+}
 
 }  // namespace kgpu

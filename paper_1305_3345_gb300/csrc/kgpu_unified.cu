@@ -57,6 +57,7 @@ struct WarpKeys {
     uint32_t* slot;       // generic pointer to the slot
     uint32_t data_saddr;  // shared-window addresses for the round-key loads
     uint32_t twk_saddr;
+    uint32_t stage_saddr;  // serving kernel: this warp's staging rows in shared memory, else 0
     int nr;
 };
 
@@ -65,6 +66,7 @@ __device__ __forceinline__ WarpKeys warp_keys(char* smem, uint32_t warp) {
     K.slot = reinterpret_cast<uint32_t*>(smem + 3 * kRegion + warp * 512);
     K.data_saddr = (uint32_t)__cvta_generic_to_shared(K.slot);
     K.twk_saddr = K.data_saddr + 256;
+    K.stage_saddr = 0;
     K.nr = 0;
     return K;
 }
@@ -501,16 +503,36 @@ __device__ __forceinline__ void quad_chains(const ReqDesc& d, uint64_t p0, uint6
 
 // Four-lane chains over pages in registered host memory: the warp moves 8
 // blocks (one 128-byte line) of each of its 8 pages at a time between the
-// buffers and its scratch area with whole-line accesses -- a four-lane load
-// straight from the pages would move a whole line over the link for 16
-// useful bytes -- and the quads run their chains on the scratch copy.  The
-// next chunk's lines are loaded from the host while the current chunk is
-// enciphered.  Scratch: two 1-KiB halves, [page of the tile][block of the
-// chunk]; pages must hold a multiple of 8 blocks.  __syncwarp orders the
-// lanes' scratch accesses.
+// buffers and its staging rows in shared memory with whole-line accesses -- a
+// four-lane load straight from the pages would move a whole line over the
+// link for 16 useful bytes -- and the quads run their chains on the staged
+// copy.  The next chunk's lines are loaded from the host while the current
+// chunk is enciphered.  sbuf: shared-window address of the warp's 8 rows of
+// kServeStageRow bytes (the 16-byte pad per row spreads both the copies'
+// 16-byte accesses and the quads' column reads over all banks).  Pages must
+// hold a multiple of 8 blocks.
+__device__ __forceinline__ void sts128(uint32_t a, const uint4& v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 template <int NR>
 __device__ __forceinline__ void quad_chains_staged(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K,
-                                                   uint4* stage) {
+                                                   uint32_t sbuf) {
     const uint32_t lane = lane_id();
     const uint32_t c = lane & 3u, base = lane & ~3u, qp = lane >> 2;
     const UniLanes L = uni_lanes(lane, 0);
@@ -522,6 +544,9 @@ __device__ __forceinline__ void quad_chains_staged(const ReqDesc& d, uint64_t p0
     // copy positions: lanes 8p..8p+7 move page p's line (pages 0-3, then 4-7)
     const uint32_t cp_blk = lane & 7u, cp_pg0 = lane >> 3, cp_pg1 = cp_pg0 + 4;
     const bool ok0 = p0 + cp_pg0 < p1, ok1 = p0 + cp_pg1 < p1;
+    const uint32_t cp0 = sbuf + cp_pg0 * (uint32_t)kServeStageRow + cp_blk * 16u;
+    const uint32_t cp1 = sbuf + cp_pg1 * (uint32_t)kServeStageRow + cp_blk * 16u;
+    const uint32_t col = sbuf + qp * (uint32_t)kServeStageRow + c * 4u;  // this lane's column of its page
     const uint4 z = make_uint4(0, 0, 0, 0);
     auto fetch = [&](uint32_t chunk, uint4& v0, uint4& v1) {
         v0 = ok0 ? d.src[(p0 + cp_pg0) * bpp + chunk + cp_blk] : z;
@@ -529,28 +554,21 @@ __device__ __forceinline__ void quad_chains_staged(const ReqDesc& d, uint64_t p0
     };
     uint4 n0, n1;
     fetch(0, n0, n1);
-    for (uint32_t ch = 0, half = 0; ch < bpp; ch += kStageBlocks, half ^= 64u) {
-        uint4* buf = stage + half;
-        buf[cp_pg0 * kStageBlocks + cp_blk] = n0;
-        buf[cp_pg1 * kStageBlocks + cp_blk] = n1;
+    for (uint32_t ch = 0; ch < bpp; ch += kStageBlocks) {
+        sts128(cp0, n0);
+        sts128(cp1, n1);
         __syncwarp();
         if (ch + kStageBlocks < bpp) fetch(ch + kStageBlocks, n0, n1);  // in flight meanwhile
-        // this lane's column of its page's blocks, two blocks ahead (the
-        // scratch copy is near: L1/L2)
-        uint32_t* col = reinterpret_cast<uint32_t*>(buf + qp * kStageBlocks) + c;
-        uint32_t q0 = col[0], q1 = col[4];
 #pragma unroll 1
         for (uint32_t i = 0; i < kStageBlocks; i++) {
-            const uint32_t cur = q0;
-            q0 = q1;
-            if (i + 2 < kStageBlocks) q1 = col[4 * (i + 2)];
-            x = quad_encrypt<NR>(x ^ cur, s1, s2, s3, L, key);
-            col[4 * i] = x;
+            x = quad_encrypt<NR>(x ^ lds32(col + 16u * i), s1, s2, s3, L, key);
+            sts32(col + 16u * i, x);
         }
         __syncwarp();
-        const uint4 o0 = buf[cp_pg0 * kStageBlocks + cp_blk], o1 = buf[cp_pg1 * kStageBlocks + cp_blk];
+        const uint4 o0 = lds128(cp0), o1 = lds128(cp1);
         if (ok0) d.dst[(p0 + cp_pg0) * bpp + ch + cp_blk] = o0;
         if (ok1) d.dst[(p0 + cp_pg1) * bpp + ch + cp_blk] = o1;
+        __syncwarp();  // the rows are refilled next
     }
 }
 
@@ -566,12 +584,12 @@ __device__ __forceinline__ void tile_cbc_enc_quad(const ReqDesc& d, uint64_t p0,
 }
 
 __device__ __forceinline__ void tile_cbc_enc_quad_staged(const ReqDesc& d, uint64_t p0, uint64_t p1,
-                                                         const WarpKeys& K, uint4* stage) {
+                                                         const WarpKeys& K, uint32_t sbuf) {
     __syncwarp();
     switch (K.nr) {
-        case 10: quad_chains_staged<10>(d, p0, p1, K, stage); break;
-        case 12: quad_chains_staged<12>(d, p0, p1, K, stage); break;
-        default: quad_chains_staged<14>(d, p0, p1, K, stage); break;
+        case 10: quad_chains_staged<10>(d, p0, p1, K, sbuf); break;
+        case 12: quad_chains_staged<12>(d, p0, p1, K, sbuf); break;
+        default: quad_chains_staged<14>(d, p0, p1, K, sbuf); break;
     }
 }
 
@@ -707,7 +725,8 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
             break;
         case KGPU_MODE_CBC_ENC:
             if (stage && (d.flags & (kDescSrcHost | kDescDstHost)) && d.unit_blocks % kStageBlocks == 0) {
-                if (QUAD && (d.flags & kDescQuad)) tile_cbc_enc_quad_staged(d, u0, u1, K, stage);
+                if (QUAD && (d.flags & kDescQuad) && K.stage_saddr)
+                    tile_cbc_enc_quad_staged(d, u0, u1, K, K.stage_saddr);
                 else tile_cbc_enc_staged(d, u0, u1, K, stage);
             } else if (QUAD && (d.flags & kDescQuad))
                 tile_cbc_enc_quad(d, u0, u1, K);
@@ -965,6 +984,8 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         return;
     }
     WarpKeys K = warp_keys(smem, warp);
+    K.stage_saddr = (uint32_t)__cvta_generic_to_shared(smem + 3 * kRegion + (THREADS / 32) * 512 +
+                                                       warp * kServeStageWarpBytes);
     uint32_t cur_sel = 0xffffffffu;
     const uint32_t gw = blockIdx.x * (THREADS / 32) + warp;
     uint4* stage = a.scratch && gw < a.scratch_warps ? a.scratch + (size_t)gw * (kStageWarpBytes / 16) : nullptr;
@@ -1071,7 +1092,7 @@ cudaError_t configure_batch_kernels() {
                                  (int)unified_smem_bytes(512));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(serve_kernel<kServeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)unified_smem_bytes(512));
+                                 (int)serve_smem_bytes());
     return e;
 }
 
@@ -1088,7 +1109,7 @@ cudaError_t launch_serve_reset(ServeDev* dev, unsigned long long* mbox, int ctas
 
 cudaError_t launch_serve(const ServeArgs& a, int threads, int grid, cudaStream_t s) {
     if (threads != kServeThreads) return cudaErrorInvalidValue;
-    serve_kernel<kServeThreads><<<grid, kServeThreads, unified_smem_bytes(kServeThreads), s>>>(a);
+    serve_kernel<kServeThreads><<<grid, kServeThreads, serve_smem_bytes(), s>>>(a);
     return cudaGetLastError();
 }
 
