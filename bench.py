@@ -710,7 +710,7 @@ def run_empty_service(ctx, kg, dev):
 def run_crossover(ctx, kg, dev):
     """The paper's proposed start-up calibration (section 4): per mode and key
     size, the request size from which the GPU is faster than the CPU.  Host-
-    resident pages: kgpu_calibrate_dispatch against a batch of one and against
+    resident pages: kgpu_calibrate_dispatch against one launch and against
     the serving ring (the library's GPU legs) with OpenSSL AES on one host core
     as the CPU leg.  Device-resident pages (AES-256-XTS): the GPU leg is one
     request through the library; the CPU would first have to copy the pages
@@ -719,7 +719,7 @@ def run_crossover(ctx, kg, dev):
     out = {"paper_context": "GTX 480 vs Core i7-930 kernel AES (ECB): GPU ahead from 8 KB (two pages)",
            "cpu_leg": "OpenSSL libcrypto 3 EVP AES (AES-NI / Arm crypto extensions), one host thread"}
     xo, pts = ctx.calibrate_dispatch()
-    out["host_pages_batch"] = {"crossover_bytes": xo["bytes"], "points": pts}
+    out["host_pages_launch"] = {"crossover_bytes": xo["bytes"], "points": pts}
     ctx.serve_start()
     try:
         xo, pts = ctx.calibrate_dispatch()

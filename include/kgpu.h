@@ -503,16 +503,19 @@ int kgpu_replay_serve_stages(kgpu_ctx *ctx, const kgpu_request *reqs, const uint
 
 /*
  * Run one request (kgpu_request, any mode) and wait for it.  The GPU leg is
- * the serving ring when kgpu_serve_start has started it, otherwise a batch of
- * one request (kgpu_submit + kgpu_poll) on a stream of the context.  The host
+ * the serving ring when kgpu_serve_start has started it, otherwise one launch
+ * of the mode's kernel on a stream of the context (the pages are read and
+ * written in place, device memory or registered host memory alike).  The host
  * leg runs the request in the calling thread; it needs src and dst flagged
  * KGPU_REQ_SRC_HOST / KGPU_REQ_DST_HOST (and KGPU_REQ_IVS_HOST for CBC), else
  * KGPU_EINVAL.  With KGPU_DISPATCH_AUTO the host leg is taken when the context
  * was created with host_dispatch = 1, the request is host-resident in that
  * sense, and its length is below the measured crossover for its mode and key
  * size (AES-128 / AES-192 and AES-256 measured as AES-128 and AES-256).
- * Validation as kgpu_submit.  timeout_ns bounds the GPU leg's wait
- * (KGPU_ETIMEDOUT; < 0 waits without limit).  *ran_on (if not NULL)
+ * Validation as kgpu_submit.  timeout_ns bounds the wait for admission to a
+ * full serving ring (KGPU_ETIMEDOUT, nothing queued; < 0 waits without
+ * limit); once the GPU has the request the call returns when it completes,
+ * since it holds the caller's pages until then.  *ran_on (if not NULL)
  * receives KGPU_DISPATCH_GPU or KGPU_DISPATCH_HOST.  Returns the request's
  * status: 0, or a negative KGPU_E* code (KGPU_ENOSYS if the host leg was
  * forced and libcrypto is not available).
@@ -522,7 +525,7 @@ int kgpu_crypt(kgpu_ctx *ctx, const kgpu_request *req, uint32_t dispatch, int64_
 /* Where kgpu_crypt's host leg stops: requests shorter than bytes[mode][k]
  * (mode KGPU_MODE_XTS..KGPU_MODE_ECB; k = 0 for AES-128, 1 for AES-256) run on
  * the host.  form: the GPU leg that was measured (KGPU_DISPATCH_FORM_*). */
-#define KGPU_DISPATCH_FORM_BATCH 1u
+#define KGPU_DISPATCH_FORM_LAUNCH 1u
 #define KGPU_DISPATCH_FORM_RING 2u
 typedef struct kgpu_crossover {
     uint64_t bytes[4][2];
@@ -544,7 +547,7 @@ typedef struct kgpu_dispatch_point {
  * Measure the crossover now: for XTS, CBC decryption, CBC encryption and
  * ECB, with AES-128 and AES-256 keys, and request sizes of 4 KiB to 4 MiB
  * (powers of two) in registered pinned host memory, time kgpu_crypt's host
- * leg and its GPU leg (the serving ring if it runs, else a batch of one) and
+ * leg and its GPU leg (the serving ring if it runs, else one launch) and
  * record, per mode and key size, the smallest size from which the GPU leg is
  * faster at every larger measured size (4 KiB if it is faster everywhere;
  * 8 MiB if the host leg is faster everywhere).  The context's table is

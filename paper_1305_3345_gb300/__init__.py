@@ -32,7 +32,7 @@ _ERRORS = {
 DISPATCH_AUTO = 0
 DISPATCH_GPU = 1
 DISPATCH_HOST = 2
-DISPATCH_FORM = {1: "batch", 2: "ring"}
+DISPATCH_FORM = {1: "launch", 2: "ring"}
 
 _lock = threading.Lock()
 _lib = None

@@ -5,8 +5,8 @@
 // GPU behind below a request size of two pages, because every GPU request
 // pays a fixed launch-and-copy cost; it proposes measuring that crossover at
 // start-up and sending smaller requests to the CPU (section 4).  This file is
-// that dispatcher.  The GPU leg is the library's own (the serving ring, or a
-// batch of one).  The host leg is a separate cipher implementation that the
+// that dispatcher.  The GPU leg is the library's own (the serving ring, or one
+// launch of the mode's kernel).  The host leg is a separate cipher implementation that the
 // library does not contain: OpenSSL's libcrypto (version 3, AES-NI or the
 // Arm cryptography extensions), loaded with dlopen at first use so that the
 // library has no link-time dependency on it.  The host leg only ever touches
@@ -172,8 +172,32 @@ uint64_t mono_ns() {
         .count();
 }
 
-// The GPU leg: the serving ring if it runs, else a batch of one.
-int gpu_leg(kgpu_ctx* ctx, const kgpu_request& q, int64_t timeout_ns) {
+// One plain launch of the mode's kernel for request d (pointers as the device
+// sees them: device memory, or registered host memory through its mapping).
+cudaError_t launch_one(const kgpu_ctx* ctx, const ReqDesc& d, const HostKey& k, cudaStream_t s) {
+    if (d.mode == KGPU_MODE_COPY) return launch_copy(d.src, d.dst, d.nblocks, d.unit_blocks, ctx->num_sms, s);
+    if (d.mode == KGPU_MODE_XTS || d.mode == KGPU_MODE_ECB) {
+        BulkParams p;
+        fill_bulk(&p, k, (int)d.dir, d.src, d.dst, d.nblocks * 16, (size_t)d.unit_blocks * 16, d.first_sector);
+        return d.mode == KGPU_MODE_XTS ? launch_xts(p, k.nr, (int)d.dir, ctx->num_sms, s)
+                                       : launch_ecb(p, k.nr, (int)d.dir, ctx->num_sms, s);
+    }
+    CbcParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.src = d.src;
+    p.dst = d.dst;
+    p.ivs = d.ivs;
+    p.npages = d.nblocks / d.unit_blocks;
+    p.bpp = d.unit_blocks;
+    const bool enc = d.mode == KGPU_MODE_CBC_ENC;
+    std::memcpy(p.rk, enc ? k.enc : k.dec, sizeof(p.rk));
+    return enc ? launch_cbc_enc(p, k.nr, ctx->num_sms, s) : launch_cbc_dec(p, k.nr, ctx->num_sms, s);
+}
+
+// The GPU leg: the serving ring if it runs, else one launch of the mode's
+// kernel waited for on an event of its own (the paper's launch, copy and wait,
+// with the pages read in place).
+int gpu_leg(kgpu_ctx* ctx, const kgpu_request& q, const ReqDesc& d, int64_t timeout_ns) {
     const uint64_t t0 = mono_ns();
     auto left = [&]() -> int64_t {
         if (timeout_ns < 0) return -1;
@@ -189,23 +213,42 @@ int gpu_leg(kgpu_ctx* ctx, const kgpu_request& q, int64_t timeout_ns) {
             std::this_thread::yield();
         }
         if (rc == KGPU_OK) {
+            // the request holds the caller's pages until it completes, and
+            // the caller has no ticket to wait on later: wait for it
             int st = 0;
-            rc = kgpu_serve_poll(ctx, t, left(), &st, nullptr);
+            rc = kgpu_serve_poll(ctx, t, -1, &st, nullptr);
             return rc ? rc : st;
         }
         if (serving(ctx)) return rc;  // refused on its own merits
-        // the ring stopped between the check and the submit: a batch instead
+        // the ring stopped between the check and the submit: a launch instead
     }
-    kgpu_ticket t = 0;
-    int st = 0;
-    int rc;
-    while ((rc = kgpu_submit(ctx, &q, 1, (kgpu_stream)ctx->crypt_stream, &t, &st)) == KGPU_EBUSY) {
-        if (timeout_ns >= 0 && left() == 0) return KGPU_ETIMEDOUT;
-        std::this_thread::yield();
+    HostKey k;
+    if (d.mode != KGPU_MODE_COPY) {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        k = ctx->keys[d.key];
+        if (!k.live) return KGPU_ENOENT;
     }
-    if (rc) return rc;
-    rc = kgpu_poll(ctx, t, left(), &st);
-    return rc ? rc : st;
+    DeviceGuard g(ctx->device);
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    cudaError_t e = launch_one(ctx, d, k, ctx->crypt_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, ctx->crypt_stream);
+    // the launch reads and writes the caller's pages: wait until it is done,
+    // spinning for the first 200 us, then sleeping between checks
+    const uint64_t spin_until = mono_ns() + 200000;
+    if (e == cudaSuccess) {
+        while ((e = cudaEventQuery(ev)) == cudaErrorNotReady)
+            if (mono_ns() > spin_until) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    return KGPU_OK;
 }
 
 int crypt(kgpu_ctx* ctx, const kgpu_request& q, uint32_t dispatch, int64_t timeout_ns, uint32_t* ran_on) {
@@ -231,7 +274,7 @@ int crypt(kgpu_ctx* ctx, const kgpu_request& q, uint32_t dispatch, int64_t timeo
         return KGPU_EINVAL;
     }
     if (ran_on) *ran_on = host ? KGPU_DISPATCH_HOST : KGPU_DISPATCH_GPU;
-    if (!host) return gpu_leg(ctx, q, timeout_ns);
+    if (!host) return gpu_leg(ctx, q, d, timeout_ns);
     HostKey k;
     if (q.mode != KGPU_MODE_COPY) {
         std::lock_guard<std::mutex> g(ctx->mu);
@@ -264,7 +307,7 @@ int kgpu_calibrate_dispatch(kgpu_ctx* ctx, kgpu_dispatch_point* points, size_t m
     if (!evp().ok) return KGPU_ENOSYS;
     constexpr uint64_t kMin = 4096, kMax = 4u << 20, kPage = 4096;
     constexpr int kModes = 4;
-    const uint32_t form = serving(ctx) ? KGPU_DISPATCH_FORM_RING : KGPU_DISPATCH_FORM_BATCH;
+    const uint32_t form = serving(ctx) ? KGPU_DISPATCH_FORM_RING : KGPU_DISPATCH_FORM_LAUNCH;
 
     // pinned, mapped host buffers (input, output, IVs), registered with the context
     unsigned char *in = nullptr, *outb = nullptr, *ivs = nullptr;

@@ -3,7 +3,7 @@ at start-up where the GPU overtakes the CPU and send smaller requests to the
 CPU).
 
 Both legs must give the oracle's bytes: the GPU leg (the library's kernels,
-through a batch of one or the serving ring) and the host leg (OpenSSL's
+through one launch or the serving ring) and the host leg (OpenSSL's
 libcrypto on registered host pages).  Routed and unrouted results are
 compared with each other and with the oracle; the router must send only
 host-resident requests below the measured crossover to the host.
@@ -95,7 +95,7 @@ def test_auto_dispatch_routes_by_the_measured_crossover():
     cfg.host_dispatch = 1
     with kg.Context(0, cfg) as c:          # calibrates at creation
         xo = c.crossover()
-        assert xo["valid"] and xo["form"] == "batch"
+        assert xo["valid"] and xo["form"] == "launch"
         for name in ("xts", "cbc_dec", "cbc_enc", "ecb"):
             for kb in ("aes128", "aes256"):
                 assert xo["bytes"][name][kb] in [4096 << i for i in range(12)]
@@ -193,4 +193,51 @@ def test_host_leg_refusals(ctx):
         assert not hp.dst.numpy().any()
     finally:
         hp.close()
+        ctx.delkey(kh)
+
+
+def test_concurrent_callers_on_both_legs(ctx):
+    """Four threads call kgpu_crypt at once, alternating the host and GPU legs
+    (each thread keeps its own OpenSSL context), with the serving ring as the
+    GPU leg; every output equals the oracle's."""
+    import threading
+    import paper_1305_3345_gb300 as kg
+    key = w.xts_key(430, 256)
+    kh = ctx.setkey(key, True)
+    nthreads, calls, size = 4, 12, 16 << 10
+    hps = [HostPages(ctx, 430 + t, calls * size) for t in range(nthreads)]
+    errors = []
+
+    def worker(t):
+        try:
+            hp = hps[t]
+            for i in range(calls):
+                leg = kg.DISPATCH_HOST if (i + t) % 2 else kg.DISPATCH_GPU
+                r = request(kg, kg.MODE_XTS, kh, hp.src.data_ptr() + i * size, hp.dst.data_ptr() + i * size,
+                            size, 4096, 1000 * t + 4 * i)
+                st, ran = ctx.crypt(r, leg, 10_000_000_000)
+                if st != 0 or ran != leg:
+                    errors.append((t, i, st, ran))
+        except Exception as e:  # surfaced below
+            errors.append((t, repr(e)))
+
+    ctx.serve_start()
+    try:
+        ths = [threading.Thread(target=worker, args=(t,)) for t in range(nthreads)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+    finally:
+        ctx.serve_stop(10_000_000_000)
+    try:
+        assert not errors, errors
+        for t, hp in enumerate(hps):
+            got = hp.dst.numpy().reshape(calls, size)
+            for i in range(calls):
+                ref = oracle.xts(key, 0, hp.data[i * size:(i + 1) * size], 4096, 1000 * t + 4 * i)
+                assert np.array_equal(got[i], ref), (t, i)
+    finally:
+        for hp in hps:
+            hp.close()
         ctx.delkey(kh)
