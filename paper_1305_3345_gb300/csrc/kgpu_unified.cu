@@ -1047,7 +1047,7 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         const unsigned long long seq = a.dslots[s].seq;
         const unsigned long long t_first = __shfl_sync(0xffffffffu, gtimer(), 0);
         if (k == 0) a.t_start[s] = t_first;  // same value from every lane
-        const int st = run_tile<true>(d, k, a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile<true, true>(d, k, a.keys, a.max_keys, K, cur_sel, stage);
         if (st) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
         // Publication: the warp barrier orders every lane's stores before
         // lane 0, lane 0's acq_rel increment releases them at GPU scope, the
