@@ -237,10 +237,10 @@ int kgpu_aes_xts_crypt_host(kgpu_ctx *ctx, kgpu_key key, int dir, const void *sr
  * Registration is per context; the caller keeps ownership of the memory.
  *
  * kgpu_host_unregister: ptr is the start of a registered range (else
- * KGPU_ENOENT).  Waits for batches submitted with kgpu_submit and for
- * requests published to the serving ring, then forgets the range.  Work the
- * caller launched with kgpu_submit_noalloc runs on the caller's stream: the
- * caller must have synchronized that stream first.
+ * KGPU_ENOENT).  Waits for batches submitted with kgpu_submit or
+ * kgpu_submit_noalloc, for requests published to the serving ring, and for
+ * kgpu_aes_xts_crypt_host and kgpu_crypt calls running on host pages, then
+ * forgets the range.
  */
 #define KGPU_HOSTREG_PIN 0u
 #define KGPU_HOSTREG_PINNED 1u

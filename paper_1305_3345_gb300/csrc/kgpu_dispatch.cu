@@ -274,7 +274,17 @@ int crypt(kgpu_ctx* ctx, const kgpu_request& q, uint32_t dispatch, int64_t timeo
         return KGPU_EINVAL;
     }
     if (ran_on) *ran_on = host ? KGPU_DISPATCH_HOST : KGPU_DISPATCH_GPU;
-    if (!host) return gpu_leg(ctx, q, d, timeout_ns);
+    if (!host) {
+        if (!(q.flags & (KGPU_REQ_SRC_HOST | KGPU_REQ_DST_HOST | KGPU_REQ_IVS_HOST)))
+            return gpu_leg(ctx, q, d, timeout_ns);
+        // host pages on the GPU: host_mu is held until the request is done,
+        // so kgpu_host_unregister (which drops a range only under it) cannot
+        // unpin them meanwhile; validated again under it
+        std::lock_guard<std::mutex> hold(ctx->host_mu);
+        RangeCache again;
+        if ((rc = make_desc(ctx, q, again, 32, &d))) return rc;
+        return gpu_leg(ctx, q, d, timeout_ns);
+    }
     HostKey k;
     if (q.mode != KGPU_MODE_COPY) {
         std::lock_guard<std::mutex> g(ctx->mu);
