@@ -160,6 +160,11 @@ int kgpu_aes_setkey(kgpu_ctx* ctx, const uint8_t* key, size_t key_len, int xts, 
         }
     }
     if (slot >= ctx->cfg.max_keys) return KGPU_ENOMEM;
+    // A running serving kernel keeps the last schedule each warp loaded,
+    // tagged with slot, direction and this generation: a new key in a freed
+    // slot carries a generation no warp has seen (0 is never issued).
+    if (++ctx->key_gen == 0) ++ctx->key_gen;
+    dk.gen = ctx->key_gen;
     DeviceGuard g(ctx->device);
     if (cudaMemcpyAsync(ctx->d_keys + slot, &dk, sizeof(dk), cudaMemcpyHostToDevice, ctx->key_stream) !=
             cudaSuccess ||

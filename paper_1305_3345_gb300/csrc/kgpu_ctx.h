@@ -123,6 +123,7 @@ struct kgpu_ctx {
     std::mutex mu;
     std::vector<kgpu::HostKey> keys;
     kgpu::DevKey* d_keys = nullptr;
+    uint32_t key_gen = 0;         // generation stamped on the last key set (under mu)
     cudaStream_t key_stream = nullptr;  // private non-blocking stream for key-table writes
 
     // host-resident pipeline (kgpu_aes_xts_crypt_host): three device staging

@@ -27,7 +27,7 @@ struct DevKey {
     uint32_t twku[kMaxRoundKeyWords];  // XTS tweak key (forward cipher)
     uint32_t nr;                       // 10, 12 or 14
     uint32_t flags;                    // kKeyLive | kKeyXts
-    uint32_t gen;                      // bumped on every setkey of the slot
+    uint32_t gen;                      // context-wide setkey count when this key was set (never 0)
     uint32_t pad;
 };
 constexpr uint32_t kKeyLive = 1u;

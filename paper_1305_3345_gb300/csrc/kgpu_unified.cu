@@ -677,9 +677,12 @@ __device__ __forceinline__ void tile_copy(const ReqDesc& d, uint64_t u0, uint64_
     for (uint64_t b = u0 * d.unit_blocks + lane_id(); b < b1; b += 32) d.dst[b] = d.src[b];
 }
 
-template <bool QUAD, bool TWO = false>
+// RESIDENT: the kernel outlives key changes (the serving kernel), so the
+// schedule a warp keeps is tagged with the key's generation as well; a batch
+// never sees one, since deleting a key waits for the batches in flight.
+template <bool QUAD, bool TWO = false, bool RESIDENT = false>
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
-                                     WarpKeys& K, uint32_t& cur_sel, uint4* stage) {
+                                     WarpKeys& K, uint32_t& cur_sel, uint32_t& cur_gen, uint4* stage) {
     const uint32_t lane = lane_id();
     if (d.mode == KGPU_MODE_COPY) {
         const uint64_t u0 = tile_in_req * d.tile_units, units = request_units(d);
@@ -693,7 +696,8 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
     if (!(flags & kKeyLive) || ((flags & kKeyXts) != 0) != is_xts) return KGPU_ENOENT;
     const int dir = (d.mode == KGPU_MODE_CBC_DEC) ? 1 : (d.mode == KGPU_MODE_CBC_ENC) ? 0 : (int)d.dir;
     const uint32_t sel = d.key * 2u + (uint32_t)dir;
-    if (sel != cur_sel) {
+    const uint32_t gen = RESIDENT ? dk.gen : 0u;
+    if (sel != cur_sel || gen != cur_gen) {
         const uint32_t* sched = dir ? dk.decu : dk.encu;
         __syncwarp();  // every lane is done with the previous key
         K.slot[lane] = sched[lane];
@@ -705,6 +709,7 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
         K.nr = (int)dk.nr;
         __syncwarp();
         cur_sel = sel;
+        cur_gen = gen;
     }
     const uint64_t units = request_units(d);
     const uint64_t u0 = tile_in_req * d.tile_units;
@@ -782,7 +787,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
     const uint32_t lane = lane_id();
     const uint32_t warp = threadIdx.x >> 5;
     WarpKeys K = warp_keys(smem, warp);
-    uint32_t cur_sel = 0xffffffffu;
+    uint32_t cur_sel = 0xffffffffu, cur_gen = 0;
     // Staged CBC encryption of host pages is compiled into the 512-thread
     // variant only: the 1024-thread variant has 64 registers per thread, and
     // the staged path would make it spill (the host side runs batches that
@@ -808,7 +813,7 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
         const uint32_t k = find_request(tile_start, nreq, t);
         const uint32_t i = order[k];
         const ReqDesc d = reqs[i];
-        const int st = run_tile<false, (THREADS <= 512)>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile<false, (THREADS <= 512)>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, cur_gen, stage);
         if (st && lane == 0) a.status[i] = st;
         if (a.fin) {
             // per-request completion: the warp that finishes a request's last
@@ -986,7 +991,7 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
     WarpKeys K = warp_keys(smem, warp);
     K.stage_saddr = (uint32_t)__cvta_generic_to_shared(smem + 3 * kRegion + (THREADS / 32) * 512 +
                                                        warp * kServeStageWarpBytes);
-    uint32_t cur_sel = 0xffffffffu;
+    uint32_t cur_sel = 0xffffffffu, cur_gen = 0;
     const uint32_t gw = blockIdx.x * (THREADS / 32) + warp;
     uint4* stage = a.scratch && gw < a.scratch_warps ? a.scratch + (size_t)gw * (kStageWarpBytes / 16) : nullptr;
     // a worker gives up on its own only if the dispatcher stopped answering
@@ -1047,7 +1052,7 @@ __global__ void __launch_bounds__(THREADS, 1) serve_kernel(const __grid_constant
         const unsigned long long seq = a.dslots[s].seq;
         const unsigned long long t_first = __shfl_sync(0xffffffffu, gtimer(), 0);
         if (k == 0) a.t_start[s] = t_first;  // same value from every lane
-        const int st = run_tile<true, true>(d, k, a.keys, a.max_keys, K, cur_sel, stage);
+        const int st = run_tile<true, true, true>(d, k, a.keys, a.max_keys, K, cur_sel, cur_gen, stage);
         if (st) *reinterpret_cast<volatile int*>(&a.status[s]) = st;
         // Publication: the warp barrier orders every lane's stores before
         // lane 0, lane 0's acq_rel increment releases them at GPU scope, the

@@ -460,3 +460,43 @@ def test_serve_stop_while_other_threads_poll(ctx):
     assert ctx.serve_poll(tk, 10_000_000_000)[0] == 0
     assert ctx.serve_stop(5_000_000_000) == 0
     t.close()
+
+
+def test_key_slot_reused_while_the_ring_runs(ctx):
+    """Keys deleted and set again while the serving kernel stays resident: each
+    round's key takes the slot the previous one left (the table hands out the
+    lowest free slot), and every request must be served with the key it names,
+    never the schedule a warp kept from the slot's previous key.  Two rounds in
+    a row use the same mode and direction, so only the key itself differs."""
+    import torch
+    import paper_1305_3345_gb300 as kg
+    n, size = 64, 16 << 10
+    data = w.seeded_bytes(611, w.STREAM_DATA, n * size)
+    ivs_np = w.page_ivs(611, n * size // 4096)
+    src = torch.from_numpy(data.copy()).cuda()
+    ivs = torch.from_numpy(ivs_np.reshape(-1).copy()).cuda()
+    dst = torch.zeros_like(src)
+    torch.cuda.synchronize()
+    ctx.serve_start()
+    try:
+        slots = set()
+        for rnd in range(20):
+            xts = (rnd // 2) % 2 == 0
+            key = w.xts_key(612 + rnd, 256) if xts else w.single_key(612 + rnd, 128)
+            kh = ctx.setkey(key, xts)
+            slots.add(kh)
+            r = np.zeros(n, dtype=kg.request_dtype())
+            r["mode"] = kg.MODE_XTS if xts else kg.MODE_CBC_ENC
+            r["key"], r["len"], r["unit_size"] = kh, size, 4096
+            r["src"] = src.data_ptr() + size * np.arange(n)
+            r["dst"] = dst.data_ptr() + size * np.arange(n)
+            r["sector"] = 4 * np.arange(n)
+            r["ivs"] = 0 if xts else ivs.data_ptr() + 16 * 4 * np.arange(n)
+            rc, _, _ = ctx.replay_serve(r, np.zeros(n, np.uint64))
+            assert rc == 0
+            ref = oracle.xts(key, 0, data, 4096, 0) if xts else oracle.cbc(key, 0, data, 4096, ivs_np)
+            assert np.array_equal(dst.cpu().numpy(), ref), rnd
+            ctx.delkey(kh)
+        assert len(slots) <= 2   # the same slot (or two) served every round
+    finally:
+        ctx.serve_stop(10_000_000_000)
