@@ -29,6 +29,14 @@ uint64_t now_ns() {
         .count();
 }
 
+// Wait for a trace's arrival time.  A sleeping thread may wake as late as the
+// kernel's timer slack (50 us by default on Linux) after its timeout, so the
+// load generators sleep only while they are far ahead and spin the rest.
+void wait_until(uint64_t target) {
+    for (uint64_t t = now_ns(); t < target; t = now_ns())
+        if (target - t > 200000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+}
+
 template <class T>
 T load_acquire(const T* p) {
     return __atomic_load_n(p, __ATOMIC_ACQUIRE);
@@ -697,12 +705,7 @@ static int replay_serve_impl(kgpu_ctx* ctx, const kgpu_request* reqs, const uint
     // with several pages ready at once would do through kgpu_serve_submit_many.
     int rc = KGPU_OK;
     for (size_t i = 0; i < n && !rc;) {
-        const uint64_t target = t0 + arrival_ns[i];
-        for (;;) {
-            const uint64_t t = now_ns();
-            if (t >= target) break;
-            if (target - t > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-        }
+        wait_until(t0 + arrival_ns[i]);
         size_t j = i;
         int r = KGPU_OK;
         {
@@ -841,10 +844,7 @@ int kgpu_replay_launches(kgpu_ctx* ctx, const kgpu_request* reqs, const uint64_t
     });
 
     for (size_t i = 0; i < n && !rc; i++) {
-        const uint64_t target = t0 + arrival_ns[i];
-        while (now_ns() < target) {
-            if (target - now_ns() > 50000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-        }
+        wait_until(t0 + arrival_ns[i]);
         if (i >= P) {  // the event slot is free once request i - P is seen complete
             while (!fin[i - P].load(std::memory_order_acquire)) {
                 if (now_ns() > deadline) {
