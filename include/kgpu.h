@@ -103,7 +103,10 @@ typedef struct kgpu_config {
 int kgpu_init(kgpu_ctx **ctx, int device, const kgpu_config *cfg);
 
 /* Stop the serving kernel if one runs, wait for the context's own work and
- * free everything the context allocated.  NULL is accepted. */
+ * free everything the context allocated.  NULL is accepted.  Completion
+ * callbacks still waiting run first, with KGPU_ENOENT for requests the
+ * stopped kernel left unfinished (no drain).  Called from a completion
+ * callback: KGPU_EINVAL, and the context stays as it was. */
 int kgpu_destroy(kgpu_ctx *ctx);
 
 /*
@@ -428,13 +431,45 @@ int kgpu_serve_submit_many(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kg
  */
 int kgpu_serve_poll(kgpu_ctx *ctx, kgpu_ticket ticket, int64_t timeout_ns, int *status, uint64_t *stamps);
 
+/*
+ * Completion callbacks (section 3.2: a service request may carry one, and its
+ * caller then blocks until the callback has run instead of busy-waiting on the
+ * response queue).  fn(arg, ticket, status) receives the request's ticket and
+ * what kgpu_serve_poll would report as its status: 0 or the request's KGPU_E*
+ * code; KGPU_ENOENT if the ring was stopped (drain limit reached) or the
+ * context destroyed before the request completed; KGPU_EIO if the serving
+ * kernel could not be relaunched while the request waited.
+ */
+typedef void (*kgpu_done_fn)(void *arg, kgpu_ticket ticket, int status);
+
+/*
+ * kgpu_serve_submit with a completion callback (fn must not be NULL).  For a
+ * request that is published -- KGPU_OK, or KGPU_EIO, for which
+ * kgpu_serve_submit also hands out a ticket -- fn is called exactly once; on
+ * any other return it is never called.  Callbacks run on the context's
+ * completion thread, started by the first such submit on a ring: one at a time,
+ * in the order the thread sees the completions (within tens of microseconds of
+ * the device's completion store), so a slow callback delays the rest.  A
+ * callback may submit, poll and set or delete keys; kgpu_serve_stop and
+ * kgpu_destroy called from a callback return KGPU_EINVAL, since both wait for
+ * the completion thread.  kgpu_serve_stop and kgpu_destroy return only after
+ * every callback of the ring has returned, so arg may be released then.  The
+ * ticket can still be polled.  Other errors as kgpu_serve_submit; KGPU_ENOMEM
+ * if the completion thread cannot be started.
+ */
+int kgpu_serve_submit_cb(kgpu_ctx *ctx, const kgpu_request *req, kgpu_done_fn fn, void *arg,
+                         kgpu_ticket *ticket);
+
 /* Wait (at most drain_timeout_ns; < 0: no limit) for every published request
  * to complete, stop the kernel and free the ring.  KGPU_ETIMEDOUT if requests
  * were still pending at the limit (the kernel is stopped all the same).  Safe
  * against other threads: submissions made once a stop has begun are refused
  * (KGPU_EINVAL); kgpu_serve_poll and kgpu_replay_serve calls still running
  * when the ring is drained return KGPU_ENOENT within about 50 us, and the ring
- * is freed only after they have; a second concurrent stop waits for the first. */
+ * is freed only after they have; a second concurrent stop waits for the first.
+ * Completion callbacks still waiting run before it returns (KGPU_ENOENT for
+ * requests the stopped kernel left unfinished).  KGPU_EINVAL when called from
+ * a completion callback. */
 int kgpu_serve_stop(kgpu_ctx *ctx, int64_t drain_timeout_ns);
 
 int kgpu_serve_get_stats(kgpu_ctx *ctx, kgpu_serve_stats *out);

@@ -12,7 +12,9 @@ wrapper that owns a kgpu_ctx.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import threading
+import traceback
 
 from . import build as _build
 
@@ -153,6 +155,7 @@ def lib() -> ctypes.CDLL:
                                   i32),
                 "kgpu_serve_start": ([vp, vp], i32),
                 "kgpu_serve_submit": ([vp, vp, ctypes.POINTER(u64)], i32),
+                "kgpu_serve_submit_cb": ([vp, vp, DONE_FN, vp, ctypes.POINTER(u64)], i32),
                 "kgpu_serve_poll": ([vp, u64, ctypes.c_int64, vp, vp], i32),
                 "kgpu_serve_stop": ([vp, ctypes.c_int64], i32),
                 "kgpu_serve_get_stats": ([vp, ctypes.POINTER(KgpuServeStats)], i32),
@@ -474,6 +477,48 @@ def kgpu_serve_submit(ctx, req) -> int:
     return t.value
 
 
+# kgpu_done_fn: void (*)(void *arg, kgpu_ticket ticket, int status)
+DONE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int)
+_done_callables = {}  # token passed as arg -> the Python callable, until it has run
+_done_tokens = itertools.count(1)
+
+
+def _done_trampoline(arg, ticket, status):
+    fn = _done_callables.pop(arg, None)
+    if fn is not None:
+        try:
+            fn(int(ticket), int(status))
+        except BaseException:  # nothing can propagate into the library's thread
+            traceback.print_exc()
+
+
+_done_c = DONE_FN(_done_trampoline)
+
+
+def kgpu_serve_submit_cb(ctx, req, fn) -> int:
+    """Publish one request with a completion callback: fn(ticket, status) is
+    called once, on the library's completion thread, when it completes (status
+    0 or a negative KGPU_E* code).  Returns the ticket; raises KgpuError like
+    kgpu_serve_submit, in which case fn is never called."""
+    import numpy as np
+    if isinstance(req, np.ndarray) or isinstance(req, np.void):
+        arr = np.ascontiguousarray(np.asarray(req, dtype=request_dtype()).reshape(1))
+        ptr = arr.ctypes.data
+        keep = arr
+    else:
+        keep = req
+        ptr = ctypes.addressof(req)
+    token = next(_done_tokens)
+    _done_callables[token] = fn
+    t = ctypes.c_uint64()
+    rc = lib().kgpu_serve_submit_cb(ctx, ptr, _done_c, token, ctypes.byref(t))
+    del keep
+    if rc not in (0, -5):  # on KGPU_EIO (-5) the request was published and fn will run
+        _done_callables.pop(token, None)
+    _check(rc, "kgpu_serve_submit_cb")
+    return t.value
+
+
 def kgpu_serve_submit_many(ctx, reqs):
     """Publish a batch of requests onto the ring in one burst; returns (rc,
     tickets of the accepted prefix).  rc is 0, or KGPU_EBUSY (-16) when the
@@ -653,6 +698,9 @@ class Context:
 
     def serve_submit(self, req) -> int:
         return kgpu_serve_submit(self.handle, req)
+
+    def serve_submit_cb(self, req, fn) -> int:
+        return kgpu_serve_submit_cb(self.handle, req, fn)
 
     def serve_poll(self, ticket, timeout_ns=-1):
         return kgpu_serve_poll(self.handle, ticket, timeout_ns)

@@ -98,7 +98,7 @@ int kgpu_init(kgpu_ctx** out, int device, const kgpu_config* cfg) {
 
 int kgpu_destroy(kgpu_ctx* ctx) {
     if (!ctx) return KGPU_OK;
-    destroy_serve(ctx);
+    if (int rc = destroy_serve(ctx)) return rc;  // called from a completion callback
     {
         DeviceGuard g(ctx->device);
         for (int i = 0; i < kgpu_ctx::kStages; i++) {

@@ -4,8 +4,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <condition_variable>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <utility>
 #include <map>
 #include <vector>
@@ -106,6 +108,13 @@ struct ServeState {
     unsigned last_exit = 0;
 };
 
+// A served request's completion callback, waiting for the request to complete.
+struct ServeCallback {
+    uint64_t seq = 0;
+    kgpu_done_fn fn = nullptr;
+    void* arg = nullptr;
+};
+
 // A host range registered with kgpu_host_register: [base, end) is page-locked
 // and mapped for the context's device, where it is seen at base + dev_off.
 struct HostRange {
@@ -154,6 +163,15 @@ struct kgpu_ctx {
     // serving loop (kgpu_serve_*)
     std::mutex serve_mu;
     kgpu::ServeState serve;
+
+    // completion callbacks of served requests (kgpu_serve_submit_cb): one
+    // thread per ring, started by the first such submit and joined before the
+    // ring is freed.  cb_mu is taken after serve_mu, never before it.
+    std::mutex cb_mu;
+    std::condition_variable cb_cv;
+    std::vector<kgpu::ServeCallback> cb_pending;  // under cb_mu
+    bool cb_stop = false;                         // under cb_mu: deliver what is left and exit
+    std::thread cb_thread;                        // started and joined under serve_mu
 
     // registered host ranges, sorted by base and disjoint
     std::mutex hreg_mu;
@@ -489,7 +507,7 @@ uint64_t order_batch(const ReqDesc* descs, uint32_t n, const Codes& codes, uint6
 }
 
 void destroy_batch_slots(kgpu_ctx* ctx);  // kgpu_batch_api.cu
-void destroy_serve(kgpu_ctx* ctx);        // kgpu_serve_api.cu
+int destroy_serve(kgpu_ctx* ctx);         // kgpu_serve_api.cu; KGPU_EINVAL on the completion thread
 // Wait until every request published to the serving ring so far has completed
 // (no-op when serving is off).  kgpu_serve_api.cu.
 int serve_quiesce(kgpu_ctx* ctx, int64_t timeout_ns);

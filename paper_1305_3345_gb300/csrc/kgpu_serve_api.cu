@@ -355,6 +355,92 @@ int publish(kgpu_ctx* ctx, ServeState& st, const ReqDesc& d, uint64_t* seq_out) 
     return r ? r : commit(ctx, st);
 }
 
+// The completion thread of kgpu_serve_submit_cb.  It scans the registered
+// callbacks for requests whose completion the device has published and runs
+// them one at a time, holding no lock.  Between scans it yields; after 200 us
+// without a completion it sleeps 20 us at a time.  While callbacks wait it
+// also relaunches the kernel if that exited with work pending, as a poll
+// would.  Told to stop (once the ring's kernel has stopped), it runs what is
+// left -- completed requests with their status, the rest with KGPU_ENOENT --
+// and exits.  The ring's mapped words stay valid meanwhile: the ring is freed
+// only after this thread has been joined.
+void callback_loop(kgpu_ctx* ctx) {
+    ServeState& st = ctx->serve;
+    std::vector<ServeCallback> ready;
+    uint64_t last_progress = now_ns(), last_check = last_progress;
+    bool failing = false;  // the kernel could not be relaunched: what waits now gets KGPU_EIO
+    for (;;) {
+        bool stop = false;
+        {
+            std::unique_lock<std::mutex> lk(ctx->cb_mu);
+            ctx->cb_cv.wait(lk, [&] { return !ctx->cb_pending.empty() || ctx->cb_stop; });
+            stop = ctx->cb_stop;
+            if (stop && ctx->cb_pending.empty()) return;
+            size_t w = 0;
+            for (size_t i = 0; i < ctx->cb_pending.size(); i++) {
+                const ServeCallback& e = ctx->cb_pending[i];
+                const uint32_t s = (uint32_t)(e.seq & (st.nslots - 1));
+                if (stop || failing || load_acquire(&st.done_seq[s]) >= e.seq + 1) ready.push_back(e);
+                else ctx->cb_pending[w++] = e;
+            }
+            ctx->cb_pending.resize(w);
+        }
+        failing = false;
+        for (const ServeCallback& e : ready) {
+            const uint32_t s = (uint32_t)(e.seq & (st.nslots - 1));
+            // an incomplete request was taken only because the ring stopped
+            // or the kernel could not be relaunched
+            int code = stop ? KGPU_ENOENT : KGPU_EIO;
+            if (load_acquire(&st.done_seq[s]) >= e.seq + 1) {
+                uint64_t v[ServeState::kStamps] = {};
+                if (!read_completed(st, e.seq, &code, v)) {  // slot since reused: failures are kept by ticket
+                    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+                    auto f = st.failed.find(e.seq);
+                    code = f != st.failed.end() ? f->second : 0;
+                }
+            }
+            e.fn(e.arg, (kgpu_ticket)(e.seq + 1), code);
+        }
+        const uint64_t t = now_ns();
+        if (!ready.empty()) last_progress = t;
+        ready.clear();
+        if (stop) continue;
+        if (t - last_check > 50000) {
+            last_check = t;
+            std::lock_guard<std::mutex> lk(ctx->serve_mu);
+            if (!st.closing) {
+                reap(st);
+                if (!st.outstanding.empty() && ensure_running(ctx, st)) failing = true;
+            }
+        }
+        if (t - last_progress > 200000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        else cpu_relax();
+    }
+}
+
+bool on_callback_thread(const kgpu_ctx* ctx) {
+    return ctx->cb_thread.joinable() && ctx->cb_thread.get_id() == std::this_thread::get_id();
+}
+
+// Join the completion thread (serve_mu held on entry and on return, released
+// meanwhile, since callbacks may take it): it runs every callback still
+// registered and exits.  The ring's kernel must have stopped.
+void stop_callbacks(kgpu_ctx* ctx, std::unique_lock<std::mutex>& lk) {
+    if (!ctx->cb_thread.joinable()) return;
+    {
+        std::lock_guard<std::mutex> g(ctx->cb_mu);
+        ctx->cb_stop = true;
+    }
+    ctx->cb_cv.notify_all();
+    std::thread t = std::move(ctx->cb_thread);
+    lk.unlock();
+    t.join();
+    lk.lock();
+    std::lock_guard<std::mutex> g(ctx->cb_mu);
+    ctx->cb_stop = false;
+    ctx->cb_pending.clear();
+}
+
 }  // namespace
 
 namespace kgpu {
@@ -379,12 +465,20 @@ int serve_quiesce(kgpu_ctx* ctx, int64_t timeout_ns) {
     }
 }
 
-void destroy_serve(kgpu_ctx* ctx) {
-    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+int destroy_serve(kgpu_ctx* ctx) {
+    std::unique_lock<std::mutex> lk(ctx->serve_mu);
+    if (on_callback_thread(ctx)) return KGPU_EINVAL;
     ServeState& st = ctx->serve;
-    if (!st.started) return;
+    if (!st.started) return KGPU_OK;
+    st.closing = st.stopping = true;  // callbacks still to run see the ring going away
     store_release(&st.hdr->stop, 1u);
+    if (st.stream) {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(st.stream);
+    }
+    stop_callbacks(ctx, lk);
     serve_free(st);
+    return KGPU_OK;
 }
 
 }  // namespace hostutil
@@ -417,6 +511,35 @@ int kgpu_serve_submit(kgpu_ctx* ctx, const kgpu_request* req, kgpu_ticket* ticke
     uint64_t seq = 0;
     r = publish(ctx, st, d, &seq);
     if (r == KGPU_OK || r == KGPU_EIO) *ticket = seq + 1;
+    return r;
+}
+
+int kgpu_serve_submit_cb(kgpu_ctx* ctx, const kgpu_request* req, kgpu_done_fn fn, void* arg, kgpu_ticket* ticket) {
+    if (!ctx || !req || !fn || !ticket) return KGPU_EINVAL;
+    if (req->len == 0) return KGPU_EINVAL;
+    ReqDesc d;
+    RangeCache rc;
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    ServeState& st = ctx->serve;
+    if (!st.started || st.closing) return KGPU_EINVAL;
+    int r = make_desc(ctx, *req, rc, st.tile_chunks, &d);
+    if (r) return r;
+    if (!ctx->cb_thread.joinable()) {
+        try {
+            ctx->cb_thread = std::thread(callback_loop, ctx);
+        } catch (...) {
+            return KGPU_ENOMEM;
+        }
+    }
+    uint64_t seq = 0;
+    r = publish(ctx, st, d, &seq);
+    if (r != KGPU_OK && r != KGPU_EIO) return r;
+    *ticket = seq + 1;
+    {
+        std::lock_guard<std::mutex> g(ctx->cb_mu);
+        ctx->cb_pending.push_back(ServeCallback{seq, fn, arg});
+    }
+    ctx->cb_cv.notify_one();
     return r;
 }
 
@@ -502,6 +625,7 @@ int kgpu_serve_poll(kgpu_ctx* ctx, kgpu_ticket ticket, int64_t timeout_ns, int* 
 int kgpu_serve_stop(kgpu_ctx* ctx, int64_t drain_timeout_ns) {
     if (!ctx) return KGPU_EINVAL;
     std::unique_lock<std::mutex> lk(ctx->serve_mu);
+    if (on_callback_thread(ctx)) return KGPU_EINVAL;  // it would wait for itself
     ServeState& st = ctx->serve;
     if (!st.started) return KGPU_OK;
     if (st.closing) {  // another thread is stopping this ring: wait until it is gone
@@ -543,6 +667,7 @@ int kgpu_serve_stop(kgpu_ctx* ctx, int64_t drain_timeout_ns) {
         std::this_thread::sleep_for(std::chrono::microseconds(20));
         lk.lock();
     }
+    stop_callbacks(ctx, lk);  // the kernel has stopped: what is left runs now
     serve_free(st);
     return rc;
 }
