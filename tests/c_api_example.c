@@ -7,12 +7,19 @@
  *   2. encrypts it with AES-128-CBC (4096-byte pages) as one batched request
  *      through kgpu_submit / kgpu_poll;
  *   3. checks that a misaligned call is refused with KGPU_EINVAL;
+ *   4. decrypts the XTS ciphertext again through the serving ring as a request
+ *      with a completion callback, blocking on a condition variable until the
+ *      callback has run (the paper's request model, section 3.2), and checks
+ *      that the plaintext came back;
  * and writes both ciphertexts to files for the test to compare.
  * usage: c_api_example key64 key16 ivs plain out_xts out_cbc
  */
+#define _POSIX_C_SOURCE 200809L
+#include <pthread.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 #include <cuda_runtime.h>
 
@@ -50,6 +57,24 @@ static int spill(const char *path, const void *p, size_t len) {
             return 1;                                                                \
         }                                                                            \
     } while (0)
+
+/* what the completion callback hands to the thread that waits for it */
+struct done {
+    pthread_mutex_t mu;
+    pthread_cond_t cv;
+    int calls, status;
+    kgpu_ticket ticket;
+};
+
+static void on_done(void *arg, kgpu_ticket ticket, int status) {
+    struct done *d = arg;
+    pthread_mutex_lock(&d->mu);
+    d->calls++;
+    d->status = status;
+    d->ticket = ticket;
+    pthread_cond_signal(&d->cv);
+    pthread_mutex_unlock(&d->mu);
+}
 
 int main(int argc, char **argv) {
     if (argc != 7) return 2;
@@ -90,6 +115,40 @@ int main(int argc, char **argv) {
 
     /* 3. a refused call launches nothing */
     if (kgpu_aes_xts_crypt(ctx, kx, KGPU_ENCRYPT, (char *)d_in + 8, d_out, 4096, 4096, 0, 0) != KGPU_EINVAL) return 5;
+
+    /* 4. back through the serving ring, waiting for the completion callback */
+    void *d_back;
+    if (cudaMalloc(&d_back, n) || cudaDeviceSynchronize()) return 3;
+    CHECK(kgpu_serve_start(ctx, NULL));
+    kgpu_request q;
+    memset(&q, 0, sizeof(q));
+    q.mode = KGPU_MODE_XTS;
+    q.dir = KGPU_DECRYPT;
+    q.key = kx;
+    q.src = d_out;
+    q.dst = d_back;
+    q.len = n;
+    q.unit_size = 4096;
+    q.sector = 5;
+    struct done dn = {PTHREAD_MUTEX_INITIALIZER, PTHREAD_COND_INITIALIZER, 0, -1, 0};
+    kgpu_ticket tq;
+    CHECK(kgpu_serve_submit_cb(ctx, &q, on_done, &dn, &tq));
+    struct timespec until;
+    clock_gettime(CLOCK_REALTIME, &until);
+    until.tv_sec += 30;
+    pthread_mutex_lock(&dn.mu);
+    while (dn.calls == 0 && pthread_cond_timedwait(&dn.cv, &dn.mu, &until) == 0) {
+    }
+    const int calls = dn.calls, status = dn.status;
+    const kgpu_ticket seen = dn.ticket;
+    pthread_mutex_unlock(&dn.mu);
+    CHECK(kgpu_serve_stop(ctx, -1));
+    if (calls != 1 || dn.calls != 1 || status != 0 || seen != tq) return 7;
+    unsigned char *back = malloc(n);
+    if (!back || cudaMemcpy(back, d_back, n, cudaMemcpyDeviceToHost)) return 3;
+    if (memcmp(back, plain, n) != 0) return 8;
+    free(back);
+    cudaFree(d_back);
 
     unsigned char *out = malloc(2 * n);
     if (!out || cudaMemcpy(out, d_out, 2 * n, cudaMemcpyDeviceToHost)) return 3;

@@ -2,7 +2,8 @@
 binding and no PyTorch on the path: compiled with gcc against include/kgpu.h
 and the in-tree libkgpu.so, run on the GPU, and its two ciphertexts (per-call
 AES-256-XTS, batched AES-128-CBC encryption) compared byte for byte with the
-oracle."""
+oracle.  The program also decrypts the XTS ciphertext through the serving ring
+with a completion callback, and checks the plaintext itself."""
 import os
 import shutil
 import subprocess
@@ -26,7 +27,7 @@ def test_c_program_through_the_abi(tmp_path):
     cuda = build.cuda_home()
     cuda_lib = os.path.join(cuda, "lib64")
     exe = str(tmp_path / "c_api_example")
-    subprocess.run([gcc, "-O2", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+    subprocess.run([gcc, "-O2", "-std=c11", "-pthread", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                     "-I", os.path.join(cuda, "include"), os.path.join(HERE, "c_api_example.c"), "-o", exe,
                     "-L", build.OUT_DIR, "-lkgpu", "-L", cuda_lib, "-lcudart",
                     f"-Wl,-rpath,{build.OUT_DIR}", f"-Wl,-rpath,{cuda_lib}"], check=True)

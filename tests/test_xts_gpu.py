@@ -94,6 +94,11 @@ def test_xts_tiny_and_single_unit(ctx):
     for du, units in ((16, 1), (4096, 1), (512, 1), (32, 3)):
         data = w.seeded_bytes(9, w.STREAM_DATA, du * units)
         assert np.array_equal(run_xts(ctx, key, ENC, data, du, 7), oracle.xts(key, ENC, data, du, 7))
+    # the last data-unit number there is (LE128 of 2^64 - 1), and units just below it
+    for du, units, first in ((4096, 1, 2**64 - 1), (512, 4, 2**64 - 4)):
+        data = w.seeded_bytes(10, w.STREAM_DATA, du * units)
+        for dir in (ENC, DEC):
+            assert np.array_equal(run_xts(ctx, key, dir, data, du, first), oracle.xts(key, dir, data, du, first))
 
 
 def test_xts_in_place(ctx):
