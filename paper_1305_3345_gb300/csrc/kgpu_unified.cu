@@ -678,8 +678,16 @@ __device__ __forceinline__ void tile_copy(const ReqDesc& d, uint64_t u0, uint64_
 }
 
 // RESIDENT: the kernel outlives key changes (the serving kernel), so the
-// schedule a warp keeps is tagged with the key's generation as well; a batch
-// never sees one, since deleting a key waits for the batches in flight.
+// schedule a warp keeps is tagged with the key's generation as well, and the
+// key record is read from L2 (ld.global.cg): the host rewrites it with a
+// copy while the kernel runs, and a line this SM's L1 kept from the slot's
+// previous key must not be taken for it.  A batch never sees a key change,
+// since deleting a key waits for the batches in flight.
+template <class T>
+__device__ __forceinline__ T key_word(const T* p, bool l2_only) {
+    return l2_only ? __ldcg(p) : *p;
+}
+
 template <bool QUAD, bool TWO = false, bool RESIDENT = false>
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
                                      WarpKeys& K, uint32_t& cur_sel, uint32_t& cur_gen, uint4* stage) {
@@ -692,21 +700,21 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
     if (d.key >= max_keys) return KGPU_ENOENT;
     const DevKey& dk = keys[d.key];
     const bool is_xts = d.mode == KGPU_MODE_XTS;
-    const uint32_t flags = dk.flags;
+    const uint32_t flags = key_word(&dk.flags, RESIDENT);
     if (!(flags & kKeyLive) || ((flags & kKeyXts) != 0) != is_xts) return KGPU_ENOENT;
     const int dir = (d.mode == KGPU_MODE_CBC_DEC) ? 1 : (d.mode == KGPU_MODE_CBC_ENC) ? 0 : (int)d.dir;
     const uint32_t sel = d.key * 2u + (uint32_t)dir;
-    const uint32_t gen = RESIDENT ? dk.gen : 0u;
+    const uint32_t gen = RESIDENT ? key_word(&dk.gen, true) : 0u;
     if (sel != cur_sel || gen != cur_gen) {
         const uint32_t* sched = dir ? dk.decu : dk.encu;
         __syncwarp();  // every lane is done with the previous key
-        K.slot[lane] = sched[lane];
-        if (lane < 28) K.slot[32 + lane] = sched[32 + lane];
+        K.slot[lane] = key_word(&sched[lane], RESIDENT);
+        if (lane < 28) K.slot[32 + lane] = key_word(&sched[32 + lane], RESIDENT);
         if (is_xts) {
-            K.slot[64 + lane] = dk.twku[lane];
-            if (lane < 28) K.slot[96 + lane] = dk.twku[32 + lane];
+            K.slot[64 + lane] = key_word(&dk.twku[lane], RESIDENT);
+            if (lane < 28) K.slot[96 + lane] = key_word(&dk.twku[32 + lane], RESIDENT);
         }
-        K.nr = (int)dk.nr;
+        K.nr = (int)key_word(&dk.nr, RESIDENT);
         __syncwarp();
         cur_sel = sel;
         cur_gen = gen;
