@@ -500,3 +500,35 @@ def test_key_slot_reused_while_the_ring_runs(ctx):
         assert len(slots) <= 2   # the same slot (or two) served every round
     finally:
         ctx.serve_stop(10_000_000_000)
+
+
+def test_pages_rewritten_by_the_host_between_requests(ctx):
+    """The same device pages reused for request after request while the ring
+    runs, their contents rewritten by a host-to-device copy in between (as page
+    buffers are reused): every request must read what the copy wrote, never
+    lines an SM kept from the previous request."""
+    import torch
+    import paper_1305_3345_gb300 as kg
+    key = w.xts_key(621, 256)
+    kh = ctx.setkey(key, True)
+    n, size = 16, 8192
+    src = torch.zeros(n * size, dtype=torch.uint8, device="cuda")
+    dst = torch.zeros_like(src)
+    r = np.zeros(n, dtype=kg.request_dtype())
+    r["mode"], r["key"], r["len"], r["unit_size"] = kg.MODE_XTS, kh, size, 4096
+    r["src"] = src.data_ptr() + size * np.arange(n)
+    r["dst"] = dst.data_ptr() + size * np.arange(n)
+    r["sector"] = 2 * np.arange(n)
+    torch.cuda.synchronize()
+    ctx.serve_start()
+    try:
+        for rnd in range(20):
+            data = w.seeded_bytes(622 + rnd, w.STREAM_DATA, n * size)
+            src.copy_(torch.from_numpy(data))     # a copy-engine write, no kernel
+            torch.cuda.synchronize()
+            rc, _, _ = ctx.replay_serve(r, np.zeros(n, np.uint64))
+            assert rc == 0
+            assert np.array_equal(dst.cpu().numpy(), oracle.xts(key, 0, data, 4096, 0)), rnd
+    finally:
+        ctx.serve_stop(10_000_000_000)
+        ctx.delkey(kh)
