@@ -179,10 +179,22 @@ int kgpu_aes_cbc_decrypt(kgpu_ctx *ctx, kgpu_key key, const void *src, void *dst
 /*
  * CBC encryption, one chain per page: C_0 = E_K(P_0 ^ IV_page),
  * C_i = E_K(P_i ^ C_{i-1}).  Sequential inside a page, parallel across pages
- * (one thread per page).  Arguments as kgpu_aes_cbc_decrypt.
+ * (one thread per page).  Arguments as kgpu_aes_cbc_decrypt.  Pages of a
+ * multiple of 128 bytes move in and out in 2-D tiles by the tensor-memory-
+ * access engine; the waits for those copies are bounded, and one that ran out
+ * (never expected) leaves the rest of that warp's pages unwritten and is
+ * counted by kgpu_bulk_wait_timeouts.
  */
 int kgpu_aes_cbc_encrypt_pages(kgpu_ctx *ctx, kgpu_key key, const void *src, void *dst, size_t len,
                                size_t page_size, const uint8_t *ivs, kgpu_stream stream);
+
+/*
+ * Bounded waits of the bulk kernels that ran out on the context's device, as
+ * a count for the whole process (the kernels' counter is per device, not per
+ * context): 0 unless a tensor copy never completed.  Synchronous: copies the
+ * counter from the device.  Errors: KGPU_EINVAL (NULL argument), KGPU_EIO.
+ */
+int kgpu_bulk_wait_timeouts(kgpu_ctx *ctx, uint32_t *count);
 
 /*
  * ECB over len / 16 independent blocks: the mode of the paper's own GPU AES

@@ -172,6 +172,7 @@ def lib() -> ctypes.CDLL:
                                               ctypes.POINTER(ctypes.c_int64)], i32),
                 "kgpu_calibrate_dispatch": ([vp, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(KgpuCrossover)], i32),
                 "kgpu_get_crossover": ([vp, ctypes.POINTER(KgpuCrossover)], i32),
+                "kgpu_bulk_wait_timeouts": ([vp, ctypes.POINTER(u32)], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -698,6 +699,11 @@ class Context:
 
     def serve_submit(self, req) -> int:
         return kgpu_serve_submit(self.handle, req)
+
+    def bulk_wait_timeouts(self) -> int:
+        n = ctypes.c_uint32()
+        _check(lib().kgpu_bulk_wait_timeouts(self.handle, ctypes.byref(n)), "kgpu_bulk_wait_timeouts")
+        return n.value
 
     def serve_submit_cb(self, req, fn) -> int:
         return kgpu_serve_submit_cb(self.handle, req, fn)

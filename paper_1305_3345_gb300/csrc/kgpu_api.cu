@@ -443,6 +443,18 @@ int kgpu_aes_cbc_encrypt_pages(kgpu_ctx* ctx, kgpu_key key, const void* src, voi
     return cbc_common(ctx, key, true, src, dst, len, page_size, ivs, stream);
 }
 
+int kgpu_bulk_wait_timeouts(kgpu_ctx* ctx, uint32_t* count) {
+    if (!ctx || !count) return KGPU_EINVAL;
+    DeviceGuard g(ctx->device);
+    unsigned int v = 0;
+    if (bulk_wait_timeouts(&v) != cudaSuccess) {
+        cudaGetLastError();
+        return KGPU_EIO;
+    }
+    *count = v;
+    return KGPU_OK;
+}
+
 int kgpu_aes_xts_crypt_host(kgpu_ctx* ctx, kgpu_key key, int dir, const void* src, void* dst, size_t len,
                             size_t du_size, uint64_t first_sector, size_t chunk_bytes) {
     int rc = xts_args(ctx, dir, len, du_size, first_sector);

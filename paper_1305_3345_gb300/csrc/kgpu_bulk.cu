@@ -9,6 +9,8 @@
 // with the warp index interleaved across CTAs, so every SM gets the same share.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "aes_device.cuh"
 #include "kgpu_bulk.h"
 
@@ -352,6 +354,122 @@ __global__ void __launch_bounds__(kCbcEncStagedThreads, 1) cbc_enc_staged_kernel
 }
 
 // ---------------------------------------------------------------------------
+// CBC encryption, staged by the tensor-memory-access engine.  The chains are
+// the same (one page per lane).  Lane 0 brings each 8-block chunk of the
+// warp's 32 pages in as one 2-D tile, 32 rows of 128 B, with 128-byte
+// swizzle: 16-byte piece i of row r lands at piece i ^ (r % 8), so that the
+// lanes' 16-byte reads of their own rows fall on distinct banks.  The lanes
+// encipher their rows in place, and lane 0 writes the tile back with one
+// tensor store, waits until the store has read the buffer, and brings in the
+// next chunk.  Neither copy passes through registers or the load/store
+// pipe.  Rows past the last page are filled with zeros on the way in and
+// clipped on the way out.  Every wait on the tile's mbarrier is bounded; a
+// wait that runs out is counted in g_bulk_wait_timeouts, the warp waits once
+// more (bounded) for its copy in flight and leaves its remaining pages
+// untouched.
+// ---------------------------------------------------------------------------
+__device__ unsigned int g_bulk_wait_timeouts;
+
+__device__ __forceinline__ bool tile_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); i++) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tile_load(uint32_t sbuf, uint64_t map, int x, int y, uint32_t bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)kTmaWarpBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(sbuf),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tile_store(uint64_t map, int x, int y, uint32_t sbuf) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(sbuf)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void tile_stores_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tile_stores_done() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <int NR>
+__global__ void __launch_bounds__(kCbcEncStagedThreads, 1) cbc_enc_tma_kernel(const __grid_constant__ CbcTmaParams p) {
+    extern __shared__ __align__(128) char smem[];
+    if (!smem_layout_ok(smem)) return;
+    const uint32_t lane = lane_id();
+    const uint32_t warp = threadIdx.x >> 5;
+    // kSmemBase + kSmemEnc + warp * 4096: 1024-byte aligned in the shared
+    // window, as the 128-byte swizzle wants
+    char* buf = smem + kSmemEnc + warp * kTmaWarpBytes;
+    const uint32_t sbuf = (uint32_t)__cvta_generic_to_shared(buf);
+    const uint32_t bar =
+        (uint32_t)__cvta_generic_to_shared(smem + kSmemEnc + kCbcEncStagedMaxWarps * kTmaWarpBytes + warp * 8);
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tensor copies see it initialised
+    }
+    fill_enc(smem);
+    __syncthreads();
+
+    const Rep4 T{lane * 4u, lane * 4u + 128u};
+    const ParamKey K{p.rk};
+    const uint32_t nchunks = p.bpp / kStageBlocks;
+    const uint64_t ngroups = (p.npages + 31) >> 5;
+    const uint64_t src_map = reinterpret_cast<uint64_t>(&p.src_map);
+    const uint64_t dst_map = reinterpret_cast<uint64_t>(&p.dst_map);
+    char* own = buf + lane * 128;  // this lane's row
+    uint32_t parity = 0;
+    bool ok = true;
+    for (uint64_t g = interleaved_warp(); ok && g < ngroups; g += total_warps()) {
+        const uint64_t page = (g << 5) + lane;
+        uint4 x = page < p.npages ? p.ivs[page] : make_uint4(0, 0, 0, 0);
+        const int y = (int)(g << 5);
+        if (lane == 0) {
+            tile_stores_read();  // the previous group's last store has read the buffer
+            tile_load(sbuf, src_map, 0, y, bar);
+        }
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            ok = __all_sync(0xffffffffu, tile_wait(bar, parity));
+            if (!ok) break;
+            parity ^= 1;
+#pragma unroll 1
+            for (int i = 0; i < kStageBlocks; i++) {
+                uint4* blk = reinterpret_cast<uint4*>(own + ((i ^ (lane & 7)) << 4));
+                const uint4 pt = *blk;
+                xor4(x, pt.x, pt.y, pt.z, pt.w);
+                encrypt_block<NR>(x.x, x.y, x.z, x.w, T, K);
+                *blk = x;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the tensor store sees the rows
+            __syncwarp();
+            if (lane == 0) {
+                tile_store(dst_map, (int)(c * 32), y, sbuf);
+                if (c + 1 < nchunks) {
+                    tile_stores_read();
+                    tile_load(sbuf, src_map, (int)((c + 1) * 32), y, bar);
+                }
+            }
+        }
+    }
+    if (!ok && lane == 0) {
+        atomicAdd(&g_bulk_wait_timeouts, 1u);
+        tile_wait(bar, parity);  // the load still in flight, bounded
+    }
+    if (lane == 0) tile_stores_done();
+}
+
+// ---------------------------------------------------------------------------
 // XTS with ciphertext stealing (IEEE 1619-2007 5.3.2 encryption, 5.4.2
 // decryption) for data units of du bytes, du >= 16 and not a multiple of 16:
 // m full blocks and a final partial block of b bytes.  One warp per data unit:
@@ -513,6 +631,49 @@ KernelFn<CbcParams> cbc_enc_staged_fn(int nr) {
     }
 }
 
+KernelFn<CbcTmaParams> cbc_enc_tma_fn(int nr) {
+    switch (nr) {
+        case 10: return cbc_enc_tma_kernel<10>;
+        case 12: return cbc_enc_tma_kernel<12>;
+        case 14: return cbc_enc_tma_kernel<14>;
+        default: return nullptr;
+    }
+}
+
+// cuTensorMapEncodeTiled, found through the runtime (no link against the
+// driver library); null if the driver does not provide it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// The pages [0, npages) of bpp blocks at base as a 2-D tensor of 32-bit words
+// read and written in boxes of 32 words (one 8-block chunk) x 32 pages.
+bool page_tile_map(CUtensorMap* m, const void* base, uint64_t npages, uint32_t bpp) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || npages > 0x7fffffffull) return false;
+    const cuuint64_t dim[2] = {(cuuint64_t)bpp * 4, (cuuint64_t)npages};
+    const cuuint64_t stride[1] = {(cuuint64_t)bpp * 16};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estride[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dim, stride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 KernelFn<CbcParams> cbc_fn(int nr, bool enc) {
     switch (nr) {
         case 10: return enc ? cbc_enc_kernel<10> : cbc_dec_kernel<10>;
@@ -523,6 +684,10 @@ KernelFn<CbcParams> cbc_fn(int nr, bool enc) {
 }
 
 }  // namespace
+
+cudaError_t bulk_wait_timeouts(unsigned int* out) {
+    return cudaMemcpyFromSymbol(out, g_bulk_wait_timeouts, sizeof(unsigned int));
+}
 
 cudaError_t configure_kernels() {
     for (int nr : {10, 12, 14}) {
@@ -540,6 +705,8 @@ cudaError_t configure_kernels() {
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(cbc_enc_staged_fn(nr), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmemEncStaged);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(cbc_enc_tma_fn(nr), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemEncTma);
         if (e != cudaSuccess) return e;
         for (int dir = 0; dir < 2; dir++) {
             e = cudaFuncSetAttribute(cts_fn(nr, dir), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -624,6 +791,23 @@ int cbc_enc_staged_warps(uint64_t groups, int num_sms) {
 }
 
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
+    if (p.bpp % kStageBlocks == 0 && p.npages) {
+        CbcTmaParams t;
+        std::memset(&t, 0, sizeof(t));
+        auto fn = cbc_enc_tma_fn(nr);
+        if (fn && page_tile_map(&t.src_map, p.src, p.npages, p.bpp) &&
+            page_tile_map(&t.dst_map, p.dst, p.npages, p.bpp)) {
+            t.ivs = p.ivs;
+            t.npages = p.npages;
+            t.bpp = p.bpp;
+            std::memcpy(t.rk, p.rk, sizeof(t.rk));
+            const uint64_t groups = (p.npages + 31) / 32;
+            const int grid = (int)(groups < (uint64_t)num_sms ? groups : num_sms);
+            const int warps = cbc_enc_staged_warps(groups, num_sms);
+            fn<<<grid, warps * 32, kSmemEncTma, s>>>(t);
+            return cudaGetLastError();
+        }
+    }
     if (p.bpp % kStageBlocks == 0) {
         auto fn = cbc_enc_staged_fn(nr);
         if (!fn) return cudaErrorInvalidValue;

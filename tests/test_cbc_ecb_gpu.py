@@ -67,6 +67,30 @@ def test_cbc_encrypt_launch_shapes(ctx, page, npages):
     assert np.array_equal(got, ref), (page, npages)
 
 
+def test_cbc_encrypt_pages_at_16_byte_offsets(ctx):
+    """Source and destination 16-byte aligned but not 128-byte aligned (the
+    tile copies need 16), several groups with a ragged last one; then no
+    bounded wait of the bulk kernels has run out in this process."""
+    import torch
+    key = w.single_key(14, 256)
+    npages = 3 * 32 + 7
+    data = w.seeded_bytes(14, w.STREAM_DATA, 4096 * npages)
+    ivs = w.page_ivs(14, npages)
+    kh = ctx.setkey(key, False)
+    try:
+        sbuf = torch.zeros(4096 * npages + 64, dtype=torch.uint8, device="cuda")
+        dbuf = torch.zeros(4096 * npages + 64, dtype=torch.uint8, device="cuda")
+        src, dst = sbuf[16:16 + 4096 * npages], dbuf[48:48 + 4096 * npages]
+        src.copy_(torch.from_numpy(data))
+        iv = to_dev(np.ascontiguousarray(ivs).reshape(-1))
+        ctx.cbc_encrypt_pages(kh, src, dst, 4096, iv)
+        assert np.array_equal(to_np(dst), oracle.cbc(key, 0, data, 4096, ivs))
+        assert not dbuf[:48].any() and not dbuf[48 + 4096 * npages:].any()   # nothing written outside
+    finally:
+        ctx.delkey(kh)
+    assert ctx.bulk_wait_timeouts() == 0
+
+
 def test_cbc_in_place(ctx):
     key = w.single_key(13, 128)
     data = w.seeded_bytes(13, w.STREAM_DATA, 4096 * 500)
