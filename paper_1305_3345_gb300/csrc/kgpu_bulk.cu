@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "aes_device.cuh"
 #include "kgpu_bulk.h"
@@ -790,19 +791,52 @@ int cbc_enc_staged_warps(uint64_t groups, int num_sms) {
     return best;
 }
 
+// The last pair of tensor maps made, for calls that repeat on the same buffers
+// (encoding one costs microseconds of host time).
+struct TileMapCache {
+    std::mutex mu;
+    bool valid = false;
+    const void* src = nullptr;
+    const void* dst = nullptr;
+    uint64_t npages = 0;
+    uint32_t bpp = 0;
+    CUtensorMap src_map, dst_map;
+};
+
+bool page_tile_maps(CbcTmaParams* t, const CbcParams& p) {
+    static TileMapCache c;
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (!(c.valid && c.src == p.src && c.dst == p.dst && c.npages == p.npages && c.bpp == p.bpp)) {
+        c.valid = page_tile_map(&c.src_map, p.src, p.npages, p.bpp) && page_tile_map(&c.dst_map, p.dst, p.npages, p.bpp);
+        if (!c.valid) return false;
+        c.src = p.src;
+        c.dst = p.dst;
+        c.npages = p.npages;
+        c.bpp = p.bpp;
+    }
+    t->src_map = c.src_map;
+    t->dst_map = c.dst_map;
+    return true;
+}
+
 cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t s) {
-    if (p.bpp % kStageBlocks == 0 && p.npages) {
+    // The tensor tiles take a seventh of the staging traffic off the
+    // shared-memory path, which pays once that path is the bound: from 12
+    // groups of 32 pages per SM (measured at 4-KiB pages: 8 groups per SM
+    // 227 us staged through registers against 232 us in tiles, 16 groups
+    // 389 against 355 us).  Below that a launch is a chain's latency either
+    // way, and the tiles' two tensor maps would only add host time.
+    const uint64_t groups = (p.npages + 31) / 32;
+    if (p.bpp % kStageBlocks == 0 && groups >= 12ull * (uint64_t)(num_sms > 0 ? num_sms : 1)) {
         CbcTmaParams t;
         std::memset(&t, 0, sizeof(t));
         auto fn = cbc_enc_tma_fn(nr);
-        if (fn && page_tile_map(&t.src_map, p.src, p.npages, p.bpp) &&
-            page_tile_map(&t.dst_map, p.dst, p.npages, p.bpp)) {
+        if (fn && page_tile_maps(&t, p)) {
             t.ivs = p.ivs;
             t.npages = p.npages;
             t.bpp = p.bpp;
             std::memcpy(t.rk, p.rk, sizeof(t.rk));
-            const uint64_t groups = (p.npages + 31) / 32;
-            const int grid = (int)(groups < (uint64_t)num_sms ? groups : num_sms);
+            const int grid = num_sms;
             const int warps = cbc_enc_staged_warps(groups, num_sms);
             fn<<<grid, warps * 32, kSmemEncTma, s>>>(t);
             return cudaGetLastError();
@@ -811,7 +845,6 @@ cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t
     if (p.bpp % kStageBlocks == 0) {
         auto fn = cbc_enc_staged_fn(nr);
         if (!fn) return cudaErrorInvalidValue;
-        const uint64_t groups = (p.npages + 31) / 32;
         const int grid = (int)(groups < (uint64_t)num_sms ? (groups ? groups : 1) : num_sms);
         const int warps = cbc_enc_staged_warps(groups, num_sms);
         fn<<<grid, warps * 32, kSmemEnc + warps * kStageWarpSmem, s>>>(p);
@@ -821,7 +854,6 @@ cudaError_t launch_cbc_enc(const CbcParams& p, int nr, int num_sms, cudaStream_t
     if (!fn) return cudaErrorInvalidValue;
     // a 32-page group is a heavy work item (32 chains of whole pages): give
     // every SM work as soon as there are as many groups as SMs
-    const uint64_t groups = (p.npages + 31) / 32;
     const int grid = (int)(groups < (uint64_t)num_sms ? (groups ? groups : 1) : num_sms);
     fn<<<grid, kBulkThreads, kSmemEnc, s>>>(p);
     return cudaGetLastError();

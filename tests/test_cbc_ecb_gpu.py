@@ -67,25 +67,30 @@ def test_cbc_encrypt_launch_shapes(ctx, page, npages):
     assert np.array_equal(got, ref), (page, npages)
 
 
-def test_cbc_encrypt_pages_at_16_byte_offsets(ctx):
+@pytest.mark.parametrize("page", [128, 4096])
+def test_cbc_encrypt_pages_at_16_byte_offsets(ctx, page):
     """Source and destination 16-byte aligned but not 128-byte aligned (the
-    tile copies need 16), several groups with a ragged last one; then no
-    bounded wait of the bulk kernels has run out in this process."""
+    tensor-tile copies need 16), with enough 32-page groups for the tile
+    kernel (12 per SM; 4-KiB pages: 240 MB) and a ragged last group; nothing
+    is written outside the destination, and no bounded wait of the bulk
+    kernels has run out in this process."""
     import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     key = w.single_key(14, 256)
-    npages = 3 * 32 + 7
-    data = w.seeded_bytes(14, w.STREAM_DATA, 4096 * npages)
-    ivs = w.page_ivs(14, npages)
+    npages = 12 * sms * 32 + 7
+    n = page * npages
+    data = w.seeded_bytes(14 + page, w.STREAM_DATA, n)
+    ivs = w.page_ivs(14 + page, npages)
     kh = ctx.setkey(key, False)
     try:
-        sbuf = torch.zeros(4096 * npages + 64, dtype=torch.uint8, device="cuda")
-        dbuf = torch.zeros(4096 * npages + 64, dtype=torch.uint8, device="cuda")
-        src, dst = sbuf[16:16 + 4096 * npages], dbuf[48:48 + 4096 * npages]
+        sbuf = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+        dbuf = torch.zeros(n + 64, dtype=torch.uint8, device="cuda")
+        src, dst = sbuf[16:16 + n], dbuf[48:48 + n]
         src.copy_(torch.from_numpy(data))
         iv = to_dev(np.ascontiguousarray(ivs).reshape(-1))
-        ctx.cbc_encrypt_pages(kh, src, dst, 4096, iv)
-        assert np.array_equal(to_np(dst), oracle.cbc(key, 0, data, 4096, ivs))
-        assert not dbuf[:48].any() and not dbuf[48 + 4096 * npages:].any()   # nothing written outside
+        ctx.cbc_encrypt_pages(kh, src, dst, page, iv)
+        assert np.array_equal(to_np(dst), oracle.cbc(key, 0, data, page, ivs))
+        assert not dbuf[:48].any() and not dbuf[48 + n:].any()   # nothing written outside
     finally:
         ctx.delkey(kh)
     assert ctx.bulk_wait_timeouts() == 0
