@@ -203,7 +203,7 @@ int prepare_slot(kgpu_ctx* ctx, kgpu::BatchSlot& s, size_t n, const kgpu_tuning&
     kp.func = const_cast<void*>(batch_kernel_fn((int)t.threads));
     kp.gridDim = dim3(t.ctas);
     kp.blockDim = dim3(t.threads);
-    kp.sharedMemBytes = (unsigned)unified_smem_bytes((int)t.threads);
+    kp.sharedMemBytes = (unsigned)batch_smem_bytes((int)t.threads);
     kp.kernelParams = kargs;
     cudaGraphNode_t deps[4] = {s.n_copy, n_ctr, s.n_status_clear, s.n_fin_clear};
     ok = ok && kp.func && cudaGraphAddKernelNode(&s.n_kernel, g, deps, 4, &kp) == cudaSuccess;

@@ -201,6 +201,20 @@ cudaError_t configure_batch_kernels();  // unified kernels: opt-in to large dyna
 // Unified-kernel shared memory: three table regions plus one 512-B key slot
 // per warp (data schedule, then the XTS tweak schedule, 240 B each).
 inline size_t unified_smem_bytes(int threads) { return 3 * kRegionBytes + (size_t)(threads / 32) * 512; }
+// The 512-thread batch kernel adds, after the key slots, a pool of staging
+// areas its warps share for CBC encryption of device pages (32 pages x 4
+// blocks, 64-byte rows), then the pool's free mask.  A warp that finds no free
+// area runs its tile without one.
+constexpr uint32_t kPoolBlocks = 4;
+constexpr size_t kPoolRow = kPoolBlocks * 16;
+constexpr size_t kPoolAreaBytes = 32 * kPoolRow;
+constexpr uint32_t kPoolAreas = 13;
+constexpr int kPoolThreads = 512;  // the batch-kernel variant that has the pool
+inline size_t batch_smem_bytes(int threads) {
+    return unified_smem_bytes(threads) + (threads == kPoolThreads ? kPoolAreas * kPoolAreaBytes + 16 : 0);
+}
+static_assert(3 * kRegionBytes + (kPoolThreads / 32) * 512 + kPoolAreas * kPoolAreaBytes + 16 <= 232448,
+              "the staging pool exceeds the 227-KB shared-memory limit");
 // The serving kernel adds, after the key slots, a staging area per warp for
 // four-lane CBC encryption of host pages: 8 pages x 8 blocks, rows padded to
 // 144 bytes so that both the whole-line copies and the column reads are free

@@ -653,6 +653,90 @@ __device__ __forceinline__ void tile_cbc_enc_staged(const ReqDesc& d, uint64_t p
     }
 }
 
+// CBC encryption of device pages through an area of the batch kernel's
+// shared staging pool.  One lane runs one page's chain; a lane's own loads and
+// stores would be 4 KiB from its neighbours', 32 lines per warp instruction.
+// Instead the warp moves 4 blocks of each of its (up to) 32 pages at a time
+// between global memory and the area -- every instruction covering 8 pages'
+// 64 contiguous bytes -- and the lanes run their chains on the area's rows.
+// Rows are 64 B with 16-byte piece i of row r stored at piece i ^ ((r/2) % 4),
+// so that both the copies (two rows per 128 bytes of banks) and a lane's reads
+// and writes of its own row are free of bank conflicts.  The next 4 blocks are
+// loaded into registers while the current ones are enciphered.  Pages must
+// hold a multiple of 4 blocks.
+__device__ __forceinline__ uint32_t pool_piece(uint32_t row, uint32_t i) {
+    return row * (uint32_t)kPoolRow + ((i ^ ((row >> 1) & 3u)) << 4);
+}
+
+__device__ __forceinline__ void tile_cbc_enc_pooled(const ReqDesc& d, uint64_t p0, uint64_t p1, const WarpKeys& K,
+                                                    char* area) {
+    __syncwarp();
+    const uint32_t lane = lane_id();
+    const UniLanes L = uni_lanes(lane, 0);
+    const uint32_t bpp = d.unit_blocks;
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    uint4 x = p0 + lane < p1 ? d.ivs[p0 + lane] : z;
+    const uint32_t cp_page = lane >> 2, cp_blk = lane & (kPoolBlocks - 1);  // copy position
+    uint4 R[4];
+    auto fetch = [&](uint32_t c) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint64_t pg = p0 + q * 8 + cp_page;
+            R[q] = pg < p1 ? d.src[pg * bpp + c + cp_blk] : z;
+        }
+    };
+    fetch(0);
+    for (uint32_t c = 0; c < bpp; c += kPoolBlocks) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) *reinterpret_cast<uint4*>(area + pool_piece(q * 8 + cp_page, cp_blk)) = R[q];
+        __syncwarp();
+        if (c + kPoolBlocks < bpp) fetch(c + kPoolBlocks);
+#pragma unroll 1
+        for (uint32_t i = 0; i < kPoolBlocks; i++) {
+            uint4* blk = reinterpret_cast<uint4*>(area + pool_piece(lane, i));
+            const uint4 pt = *blk;
+            xor4(x, pt.x, pt.y, pt.z, pt.w);
+            cipher_block(x, K.data_saddr, K.nr, L, 0);
+            *blk = x;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint64_t pg = p0 + q * 8 + cp_page;
+            const uint4 v = *reinterpret_cast<const uint4*>(area + pool_piece(q * 8 + cp_page, cp_blk));
+            if (pg < p1) d.dst[pg * bpp + c + cp_blk] = v;
+        }
+        __syncwarp();  // the rows are refilled next
+    }
+}
+
+// Take a free area of the pool (warp-uniform result; -1 when all are in
+// use) and give it back.  The mask lives after the areas.
+__device__ __forceinline__ int pool_take(uint32_t* mask) {
+    int a = -1;
+    if (lane_id() == 0) {
+        for (uint32_t tries = 0; tries < kPoolAreas; tries++) {
+            const uint32_t m = *reinterpret_cast<volatile uint32_t*>(mask);
+            const uint32_t free = ~m & ((1u << kPoolAreas) - 1u);
+            if (!free) break;
+            const uint32_t bit = free & (0u - free);
+            if (!(atomicOr(mask, bit) & bit)) {
+                a = __ffs(bit) - 1;
+                break;
+            }
+        }
+    }
+    return __shfl_sync(0xffffffffu, a, 0);
+}
+
+__device__ __forceinline__ void pool_give(uint32_t* mask, int a) {
+    __syncwarp();
+    if (lane_id() == 0) {
+        __threadfence_block();  // the warp's accesses to the area come first
+        atomicAnd(mask, ~(1u << a));
+    }
+}
+
 // Tile t of the batch -> (request, first unit, end unit).
 __device__ __forceinline__ uint32_t find_request(const uint64_t* tile_start, uint32_t nreq, uint64_t t) {
     uint32_t lo = 0, hi = nreq;  // tile_start[lo] <= t < tile_start[hi]
@@ -690,7 +774,8 @@ __device__ __forceinline__ T key_word(const T* p, bool l2_only) {
 
 template <bool QUAD, bool TWO = false, bool RESIDENT = false>
 __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, const DevKey* keys, uint32_t max_keys,
-                                     WarpKeys& K, uint32_t& cur_sel, uint32_t& cur_gen, uint4* stage) {
+                                     WarpKeys& K, uint32_t& cur_sel, uint32_t& cur_gen, uint4* stage,
+                                     char* pool = nullptr) {
     const uint32_t lane = lane_id();
     if (d.mode == KGPU_MODE_COPY) {
         const uint64_t u0 = tile_in_req * d.tile_units, units = request_units(d);
@@ -741,10 +826,20 @@ __device__ __forceinline__ int run_tile(const ReqDesc& d, uint64_t tile_in_req, 
                 if (QUAD && (d.flags & kDescQuad) && K.stage_saddr)
                     tile_cbc_enc_quad_staged(d, u0, u1, K, K.stage_saddr);
                 else tile_cbc_enc_staged(d, u0, u1, K, stage);
-            } else if (QUAD && (d.flags & kDescQuad))
+            } else if (QUAD && (d.flags & kDescQuad)) {
                 tile_cbc_enc_quad(d, u0, u1, K);
-            else
+            } else if (pool && !(d.flags & (kDescSrcHost | kDescDstHost)) && d.unit_blocks % kPoolBlocks == 0) {
+                uint32_t* mask = reinterpret_cast<uint32_t*>(pool + kPoolAreas * kPoolAreaBytes);
+                const int a = pool_take(mask);
+                if (a >= 0) {
+                    tile_cbc_enc_pooled(d, u0, u1, K, pool + a * kPoolAreaBytes);
+                    pool_give(mask, a);
+                } else {
+                    tile_cbc_enc(d, u0, u1, K);
+                }
+            } else {
                 tile_cbc_enc(d, u0, u1, K);
+            }
             break;
         default: return KGPU_EINVAL;
     }
@@ -789,6 +884,9 @@ template <int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant__ BatchArgs a) {
     extern __shared__ __align__(128) char smem[];
     if (!smem_layout_ok(smem)) return;
+    // the 512-thread variant's staging pool for CBC encryption of device pages
+    char* pool = THREADS == kPoolThreads ? smem + 3 * kRegion + (THREADS / 32) * 512 : nullptr;
+    if (pool && threadIdx.x == 0) *reinterpret_cast<uint32_t*>(pool + kPoolAreas * kPoolAreaBytes) = 0u;
     fill_unified(smem);
     __syncthreads();
 
@@ -821,7 +919,8 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(const __grid_constant
         const uint32_t k = find_request(tile_start, nreq, t);
         const uint32_t i = order[k];
         const ReqDesc d = reqs[i];
-        const int st = run_tile<false, (THREADS <= 512)>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, cur_gen, stage);
+        const int st = run_tile<false, (THREADS <= 512)>(d, t - tile_start[k], a.keys, a.max_keys, K, cur_sel, cur_gen, stage,
+                                                           pool);
         if (st && lane == 0) a.status[i] = st;
         if (a.fin) {
             // per-request completion: the warp that finishes a request's last
@@ -1099,10 +1198,10 @@ cudaError_t upload_unified_tables(const uint32_t* te0, const uint32_t* td0, cons
 
 cudaError_t configure_batch_kernels() {
     cudaError_t e = cudaFuncSetAttribute(batch_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)unified_smem_bytes(1024));
+                                         (int)batch_smem_bytes(1024));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(batch_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)unified_smem_bytes(512));
+                                 (int)batch_smem_bytes(512));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(serve_kernel<kServeThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)serve_smem_bytes());
@@ -1152,8 +1251,8 @@ cudaError_t launch_copy(const uint4* src, uint4* dst, uint64_t nblocks, uint32_t
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int threads, int grid, cudaStream_t s) {
-    if (threads == 1024) batch_kernel<1024><<<grid, 1024, unified_smem_bytes(1024), s>>>(a);
-    else if (threads == 512) batch_kernel<512><<<grid, 512, unified_smem_bytes(512), s>>>(a);
+    if (threads == 1024) batch_kernel<1024><<<grid, 1024, batch_smem_bytes(1024), s>>>(a);
+    else if (threads == 512) batch_kernel<512><<<grid, 512, batch_smem_bytes(512), s>>>(a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
