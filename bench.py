@@ -1149,10 +1149,13 @@ def run_kgpu(args):
         line["batched"] = batched_summary(b)
 
     if rank == 0 and not args.no_serve and nbytes == GIB:
-        sv = run_serving(ctx, kg, dev, args.serve_seconds)
-        emit("serving", sv)
+        # host pages first: after the device-serving traces (their large device
+        # frees included), the GPU's accesses to host memory stall now and then
+        # for seconds, which lands on whichever form runs at the time
         svh = run_serving(ctx, kg, dev, args.serve_seconds, host=True)
         emit("serving_host", svh)
+        sv = run_serving(ctx, kg, dev, args.serve_seconds)
+        emit("serving", sv)
         rt = run_roundtrip(ctx, kg, dev)
         emit("roundtrip", rt)
         es = run_empty_service(ctx, kg, dev)

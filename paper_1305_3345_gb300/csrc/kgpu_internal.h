@@ -130,14 +130,17 @@ struct ServeSlot {
 };
 static_assert(sizeof(ServeSlot) == 128, "slot layout");
 
+// The host's words and the kernel's words sit on lines of their own: the
+// dispatcher polls `head` while it stores its heartbeat, and one shared line
+// would move between the host's cache and the device at every store.
 struct ServeHostHdr {
-    unsigned long long head;       // requests published (host writes, release)
-    unsigned int stop;             // host asks the kernel to exit
+    alignas(128) unsigned long long head;  // requests published (host writes, release)
+    unsigned int stop;                     // host asks the kernel to exit
     unsigned int pad0;
-    unsigned long long exit_code;  // kernel writes why it exited (kServeExit*)
-    unsigned long long heartbeat;  // dispatcher's last %globaltimer
-    unsigned long long pad[4];
+    alignas(128) unsigned long long exit_code;  // kernel writes why it exited (kServeExit*)
+    unsigned long long heartbeat;               // dispatcher's last %globaltimer
 };
+static_assert(sizeof(ServeHostHdr) == 256, "ring header: two 128-byte lines");
 constexpr unsigned kServeExitStop = 1, kServeExitIdle = 2, kServeExitLifetime = 3;
 
 // Each counter sits on its own 128-byte line: idle workers poll tile_head

@@ -77,7 +77,7 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     const uint64_t idle = c.idle_timeout_ns ? c.idle_timeout_ns : ctx->cfg.idle_timeout_ns;
     const uint64_t life = c.lifetime_ns ? c.lifetime_ns : 30000000000ull;
 
-    const size_t o_slots = 128;
+    const size_t o_slots = sizeof(ServeHostHdr);
     const size_t o_done = o_slots + (size_t)S * sizeof(ServeSlot);
     const size_t o_status = o_done + (size_t)S * 8;
     const size_t o_stamps = align_up(o_status + (size_t)S * 4, 128);  // kStamps arrays of S words
