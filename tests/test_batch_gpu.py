@@ -117,6 +117,23 @@ def test_mixed_batch_unit_sizes(ctx, unit):
     b.close()
 
 
+def test_cbc_encryption_batch_oversubscribes_the_staging_pool(ctx):
+    """A batch of CBC encryption only, of 512-byte pages, with several thousand
+    32-page tiles: every warp of the 512-thread kernel runs such a tile at
+    once, so some stage through the shared pool's areas and the others find
+    none free and run without one.  Every request is the oracle's."""
+    b = Batch(ctx, 41, 600, 64 << 10, 256 << 10, 8, unit=512, modes=(0.0, 0.0, 1.0), ecb=0.0)
+    ctx.set_tuning(512, 0, 0)  # the variant with the pool
+    try:
+        assert int((b.sizes // 512).sum()) // 32 > 152 * 16   # more tiles than warps
+        run(ctx, b.reqs)
+        for i in range(len(b.reqs)):
+            assert np.array_equal(b.got(i), b.expected(i)), i
+    finally:
+        ctx.set_tuning(0, 0, 0)
+        b.close()
+
+
 @pytest.mark.parametrize("threads,tile", [(512, 1), (1024, 8), (512, 128), (1024, 1024)])
 def test_tuning_shapes_give_same_bytes(ctx, threads, tile):
     b = Batch(ctx, seed=47, n=60, lo=4096, hi=512 << 10, nkeys=8)
