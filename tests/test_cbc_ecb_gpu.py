@@ -96,6 +96,20 @@ def test_cbc_encrypt_pages_at_16_byte_offsets(ctx, page):
     assert ctx.bulk_wait_timeouts() == 0
 
 
+def test_cbc_encrypt_in_place_in_tensor_tiles(ctx):
+    """In-place CBC encryption with enough 32-page groups for the tensor-tile
+    kernel (each chunk is stored back over itself before the next one is
+    loaded), ragged last group."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    key = w.single_key(15, 128)
+    npages = 12 * sms * 32 + 19
+    data = w.seeded_bytes(15, w.STREAM_DATA, 128 * npages)
+    ivs = w.page_ivs(15, npages)
+    c = run_cbc(ctx, key, True, data, 128, ivs, in_place=True)
+    assert np.array_equal(c, oracle.cbc(key, 0, data, 128, ivs))
+
+
 def test_cbc_in_place(ctx):
     key = w.single_key(13, 128)
     data = w.seeded_bytes(13, w.STREAM_DATA, 4096 * 500)
