@@ -382,7 +382,7 @@ int kgpu_autotune(kgpu_ctx *ctx, const kgpu_request *reqs, size_t n, kgpu_stream
 
 typedef struct kgpu_serve_config {
     uint32_t ring_slots;       /* ring capacity, power of two (0: the context's ring_slots) */
-    uint32_t tile_chunks;      /* XTS/ECB tile in 512-byte chunks (0: 4, i.e. 2 KiB); requests
+    uint32_t tile_chunks;      /* XTS/ECB tile in 512-byte chunks (0: 2, i.e. 1 KiB); requests
                                   published while the ring is backed up (the request
                                   published a quarter of the ring earlier still running)
                                   use at least 64 (32 KiB) for throughput */

@@ -68,10 +68,12 @@ int serve_alloc(kgpu_ctx* ctx, ServeState& st, const kgpu_serve_config* cfg) {
     uint32_t S = c.ring_slots ? c.ring_slots : ctx->cfg.ring_slots;
     if (S < 2 || (S & (S - 1)) || S > (1u << 20)) return KGPU_EINVAL;
     st.nslots = S;
-    // 2-KiB tiles when the ring keeps up: a lone request's pages spread over
-    // more warps (measured XTS p50 at 100k requests/s: 4 KiB 21.7 us, 2 KiB
-    // 18.3, 1 KiB 16.4); under backlog stage() switches to 32-KiB tiles
-    st.tile_chunks = c.tile_chunks ? c.tile_chunks : 4;
+    // 1-KiB tiles when the ring keeps up: a lone request's pages spread over
+    // more warps, each running its tile in one two-block step (one-at-a-time
+    // 4-KiB XTS round trip p50: 2-KiB tiles 13.1 us, 1 KiB 11.4, 512 B 11.3;
+    // XTS p50 at 100k requests/s 15.1, 13.6, 14.2 us); under backlog stage()
+    // switches to 32-KiB tiles
+    st.tile_chunks = c.tile_chunks ? c.tile_chunks : 2;
     if (st.tile_chunks > (1u << 20)) return KGPU_EINVAL;
     st.admit_bytes = c.admit_bytes ? c.admit_bytes : ctx->cfg.admit_bytes;
     const uint64_t idle = c.idle_timeout_ns ? c.idle_timeout_ns : ctx->cfg.idle_timeout_ns;
