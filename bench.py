@@ -926,10 +926,25 @@ def run_kgpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
 
+    def emit(section, obj):
+        # secondary measurements go on lines of their own, before the headline
+        # (no "metric" key): the headline stays the last, short line
+        if rank == 0:
+            print(json.dumps({"section": section, **obj}), flush=True)
+
     ctx = kg.Context(dev)
+    nbytes = args.bytes - args.bytes % SECTOR
+    svh = None
+    if rank == 0 and not args.no_serve and nbytes == GIB:
+        # The host-pages serving traces run first, before anything else in the
+        # process: later on, after the other sections' traffic and large
+        # allocations, the GPU's accesses to host memory stall now and then
+        # for milliseconds (on whichever form runs at the time), while the
+        # same traces in a fresh process run clean.
+        svh = run_serving(ctx, kg, dev, args.serve_seconds, host=True)
+        emit("serving_host", svh)
     key = w.xts_key(2, 256)
     kh = ctx.setkey(key, True)
-    nbytes = args.bytes - args.bytes % SECTOR
     src = torch.from_numpy(w.seeded_bytes(2, w.STREAM_DATA, nbytes)).to(f"cuda:{dev}")
     dst = torch.empty_like(src)
 
@@ -1019,12 +1034,6 @@ def run_kgpu(args):
     roofline_hbm = {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved_hbm / hbm_peak, "traffic": traffic,
                     "peak_source": "measured hbm_gbs" if peaks else "fallback 6.8 TB/s"}
-
-    def emit(section, obj):
-        # secondary measurements go on lines of their own, before the headline
-        # (no "metric" key): the headline stays the last, short line
-        if rank == 0:
-            print(json.dumps({"section": section, **obj}), flush=True)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -1173,11 +1182,6 @@ def run_kgpu(args):
         line["batched"] = batched_summary(b)
 
     if rank == 0 and not args.no_serve and nbytes == GIB:
-        # host pages first: after the device-serving traces (their large device
-        # frees included), the GPU's accesses to host memory stall now and then
-        # for seconds, which lands on whichever form runs at the time
-        svh = run_serving(ctx, kg, dev, args.serve_seconds, host=True)
-        emit("serving_host", svh)
         sv = run_serving(ctx, kg, dev, args.serve_seconds)
         emit("serving", sv)
         rt = run_roundtrip(ctx, kg, dev)
