@@ -1190,11 +1190,7 @@ def run_kgpu(args):
         emit("empty_service", es)
         line["serving"] = serving_summary(sv, svh, rt, es)
         emit("ecb_size_sweep", run_ecb_sweep(ctx, kg, dev))
-        xo = run_crossover(ctx, kg, dev)
-        emit("crossover", xo)
-        line["serving"]["crossover_host_ring_bytes"] = {
-            m: [xo["host_pages_ring"]["crossover_bytes"][m][k] for k in ("aes128", "aes256")]
-            for m in ("xts", "cbc_dec", "cbc_enc", "ecb")}
+        emit("crossover", run_crossover(ctx, kg, dev))
 
     if rank == 0 and not args.no_host and nbytes == GIB:
         emit("host_stream", run_host_stream(ctx, kg, kh, dev))
