@@ -8,8 +8,11 @@
 // run of whole pages of one CBC-decrypt request, or up to 32 pages of one
 // CBC-encrypt request -- one chain per lane).  Warps pull tile indices from a
 // global counter, map them to their request by binary search over the tile
-// prefix, load that request's key schedule into registers when it changes,
-// and run the tile.
+// prefix, copy that request's key schedule into the warp's key slot in shared
+// memory when it changes (each round then reads its key with one broadcast
+// load), and run the tile.  The 512-thread batch kernel also holds a pool of
+// shared staging areas that CBC-encryption tiles of device pages move their
+// pages through.
 #include <cuda_runtime.h>
 
 #include <algorithm>
