@@ -1,12 +1,16 @@
 // Bulk device-resident kernels: XTS (IEEE 1619), ECB, CBC decrypt (parallel
 // over blocks) and CBC encrypt (parallel over pages).
 //
-// All four share one structure: one CTA of 1024 threads per SM fills its
-// replicated lookup tables into shared memory once (see aes_device.cuh), then
-// every warp walks its own contiguous range of the buffer 32 blocks (512 B)
-// at a time, one 16-byte block per lane, so each warp-wide load and store is a
-// fully coalesced 512-byte transaction.  The work is split evenly over warps
-// with the warp index interleaved across CTAs, so every SM gets the same share.
+// All share one structure: one CTA per SM fills its replicated lookup tables
+// into shared memory once (see aes_device.cuh).  For XTS, ECB and CBC
+// decryption 1024 threads then walk their own contiguous ranges of the buffer
+// 32 blocks (512 B) at a time, one 16-byte block per lane, so each warp-wide
+// load and store is a fully coalesced 512-byte transaction; the work is split
+// evenly over warps with the warp index interleaved across CTAs, so every SM
+// gets the same share.  CBC encryption runs one page's chain per lane, 32
+// pages per warp, with the warp count set by the page count, and moves the
+// pages through shared memory in whole lines (register-staged, or as tensor
+// tiles for large launches).
 #include <cuda_runtime.h>
 
 #include <cstring>
