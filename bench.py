@@ -188,9 +188,9 @@ def measured_peaks():
         return None
 
 
-def cpu_oracle_rate(target_s: float = 10.0):
+def cpu_oracle_rate(target_s: float = 15.0):
     """Oracle AES-256-XTS GB/s on a bounded sample of the same workload (the
-    first sectors of the seed-2 buffer), on all host cores."""
+    first sectors of the seed-2 buffer, up to all of it), on all host cores."""
     import oracle
     key = w.xts_key(2, 256)
     nthreads = oracle.default_threads()
@@ -200,7 +200,7 @@ def cpu_oracle_rate(target_s: float = 10.0):
     oracle.xts(key, 0, data, SECTOR, 0, nthreads=nthreads)
     dt = time.perf_counter() - t0
     rate = size / dt
-    size = int(min(512 << 20, max(16 << 20, rate * target_s)) // SECTOR * SECTOR)
+    size = int(min(GIB, max(16 << 20, rate * target_s)) // SECTOR * SECTOR)
     data = w.seeded_bytes(2, w.STREAM_DATA, size)
     t0 = time.perf_counter()
     oracle.xts(key, 0, data, SECTOR, 0, nthreads=nthreads)
