@@ -254,10 +254,13 @@ def run_reference(args):
 # ------------------------------------------------------------------ batched and serving workloads
 
 def pct(lat_ns):
+    """Nearest-rank p50/p99/p99.9 and max (us) of latencies in ns.  The rank
+    ceil(p/100 * n) is taken in integers (p in tenths of a percent), since in
+    floating point 99.9/100 * 1000 comes out just above 999."""
     a = np.sort(np.asarray(lat_ns, dtype=np.float64)) / 1e3
     if not len(a):
         return None
-    q = lambda p: float(a[min(len(a) - 1, int(np.ceil(p / 100 * len(a))) - 1)])
+    q = lambda p: float(a[max(1, -(-round(p * 10) * len(a) // 1000)) - 1])
     return {"p50_us": q(50), "p99_us": q(99), "p99.9_us": q(99.9), "max_us": float(a[-1])}
 
 
