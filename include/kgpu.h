@@ -289,7 +289,7 @@ typedef struct kgpu_request {
 
 /* Launch shape of the persistent batch kernel (see kgpu_autotune). */
 typedef struct kgpu_tuning {
-    uint32_t threads;      /* threads per CTA: 512 or 1024 (default 1024); a batch holding
+    uint32_t threads;      /* threads per CTA: 512 or 1024 (default 512); a batch holding
                               CBC encryption of host pages runs with 512, the kernel
                               that stages those pages through whole-line copies */
     uint32_t tile_chunks;  /* work per XTS/ECB tile in 512-byte chunks (default 32 = 16 KiB);

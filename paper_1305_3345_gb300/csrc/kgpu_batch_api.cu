@@ -19,8 +19,8 @@ namespace {
 
 kgpu_tuning default_tuning(const kgpu_ctx* ctx) {
     kgpu_tuning t{};
-    t.threads = 1024;
-    t.tile_chunks = 32;
+    t.threads = kBatchDefaultThreads;
+    t.tile_chunks = kBatchDefaultTileChunks;
     t.ctas = (uint32_t)ctx->num_sms;
     return t;
 }

@@ -119,8 +119,8 @@ extern "C" int kgpu_submit_noalloc(kgpu_ctx* ctx, const kgpu_request* reqs, size
     // before its validation
     std::lock_guard<std::mutex> blk(ctx->batch_mu);
     const kgpu_tuning t = ctx->tune;
-    uint32_t threads = t.threads ? t.threads : 1024;
-    const uint32_t tile_chunks = t.tile_chunks ? t.tile_chunks : 32;
+    uint32_t threads = t.threads ? t.threads : kBatchDefaultThreads;
+    const uint32_t tile_chunks = t.tile_chunks ? t.tile_chunks : kBatchDefaultTileChunks;
     const uint32_t ctas = t.ctas ? t.ctas : (uint32_t)ctx->num_sms;
     // CBC encryption of host pages is staged only in the 512-thread kernel
     if (threads > 512 && needs_staging(reqs, n)) threads = 512;
