@@ -638,8 +638,10 @@ int kgpu_get_crossover(kgpu_ctx *ctx, kgpu_crossover *out);
  * nothing launched.  Validation as kgpu_submit (req_status, if not NULL,
  * receives each request's validation code).  kgpu_aes_delkey and
  * kgpu_host_unregister wait for batches queued here before they remove a key
- * or a range, as they do for kgpu_submit.  A batch holding CBC encryption of
- * host pages runs the 512-thread kernel, whose first
+ * or a range, as they do for kgpu_submit.  Batches run the launch shape set
+ * with kgpu_set_tuning, else 512 threads and 16-KiB tiles, as kgpu_submit's
+ * do.  A batch holding CBC encryption of host pages always runs the
+ * 512-thread kernel, whose first
  * KGPU_NOALLOC_STAGE_WARPS warps stage those pages; the other warps run them
  * one lane per page (the same bytes, more link transfers).  The counter and
  * status words are cleared on every call, but every call shares the one
